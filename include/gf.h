@@ -1,0 +1,220 @@
+/*
+ * gf.h -- C ABI of the GB300 lattice gauge-fixing library (libgf.so).
+ *
+ * The library implements the checkerboard relaxation family of Schroeck &
+ * Vogt, "Coulomb, Landau and Maximally Abelian Gauge Fixing in Lattice QCD
+ * with Multi-GPUs" (arXiv:1212.5221): the gauge functionals and the gauge
+ * precision theta of Sec. 2.1, the local SU(2)-subgroup updates of Sec. 2.2
+ * (relaxation, overrelaxation, microcanonical, stochastic relaxation), the
+ * simulated annealing of Sec. 2.3 and the sweep of Alg. 1 (Sec. 2.4), on one
+ * GPU.
+ *
+ * Conventions for every entry point:
+ *  - The return value is a status code (GF_OK = 0 or one of the GF_E*
+ *    codes below); gf_strerror() names it and gf_last_error() gives the
+ *    message of the calling thread's last failure.  No C++ exception crosses
+ *    this interface.
+ *  - dims = {Nt, Nx, Ny, Nz}: every extent even and >= 2, periodic
+ *    boundaries, mu = 0 the temporal direction.  A site's index is
+ *    s = ((t*Nx + x)*Ny + y)*Nz + z; its parity is (t+x+y+z) mod 2.
+ *  - Host link arrays use the natural "StandardPattern" order of Sec. 4.2.1:
+ *    t, x, y, z, mu, i, j, re/im -- 18 doubles per link, 72*V doubles per
+ *    lattice.  Host pointers are borrowed for the duration of the call only.
+ *  - A context owns n_copies independent lattices of the same extents (a
+ *    batch of Gribov copies, Sec. 1 and 6.6).  Every F / theta output is an
+ *    array of n_copies doubles (per-slice outputs: n_copies*Nt doubles).
+ *    Results are FP64 whatever the storage precision.
+ *  - Work is issued on the context's CUDA stream; every call returns after
+ *    its work on that stream has completed.
+ *  - A context must not be used from two threads at the same time.
+ */
+#ifndef GF_H
+#define GF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gf_ctx gf_ctx;
+
+/* Target gauge (Sec. 2.1): Landau sums over all four directions, Coulomb over
+ * the spatial ones with every time-slice an independent problem, MAG is the
+ * maximally Abelian gauge of Eq. MAG_functional. */
+typedef enum { GF_LANDAU = 0, GF_COULOMB = 1, GF_MAG = 2 } gf_gauge;
+
+/* Storage/arithmetic precision.  GF_MIXED stores links in FP32 (12 reals,
+ * Sec. 4.2) for the bulk of the sweeps and switches to FP64 storage for the
+ * final sweeps (see gf_promote / gf_fix); reductions and re-unitarisation are
+ * always FP64.  GF_MIXED is not the paper's "MP" (Sec. 4.5). */
+typedef enum { GF_FP64 = 0, GF_FP32 = 1, GF_MIXED = 2 } gf_precision;
+
+/* Local update (Step 1 of Alg. 1): relaxation (Eq. localsolution per SU(2)
+ * subgroup), overrelaxation g -> g^omega to first order (Sec. 2.2.3, the
+ * OrUpdate figure of App. A), microcanonical g -> g^2 (Sec. 2.2.4),
+ * stochastic relaxation (Sec. 2.2.5), simulated-annealing heat bath
+ * (Sec. 2.3). */
+typedef enum { GF_RELAX = 0, GF_OR = 1, GF_MICRO = 2, GF_SR = 3, GF_SA = 4 } gf_algo;
+
+enum {
+  GF_OK = 0,
+  GF_EINVAL = 1,     /* bad argument: odd/zero extent, bad enum, omega not in [1,2], T <= 0, ... */
+  GF_ENOMEM = 2,     /* device memory could not be allocated, or an external buffer is too small */
+  GF_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+  GF_ETIMEOUT = 4,   /* a bounded wait expired */
+  GF_ENOTCONV = 5,   /* gf_fix: the sweep limit was reached before theta_target */
+  GF_ENOSYS = 6      /* the library was built without a usable CUDA device */
+};
+
+/* Bytes of device memory a context needs (links in the storage layout,
+ * reduction scratch, slice flags and a bounded host-transfer staging area).
+ * Used for admission by HBM footprint and to size gf_create_ext buffers. */
+int gf_footprint(const int dims[4], int n_copies, gf_gauge gauge, gf_precision prec, size_t* bytes);
+
+/* Create a context with one lattice (n_copies = 1).  stream: a cudaStream_t
+ * to issue work on, or NULL for a stream the context creates and owns.  The
+ * links start as the unit field. */
+int gf_create(const int dims[4], gf_gauge gauge, gf_precision prec, void* stream, gf_ctx** out);
+
+/* Create a context with n_copies independent lattices (batched launches). */
+int gf_create_batch(const int dims[4], int n_copies, gf_gauge gauge, gf_precision prec, void* stream,
+                    gf_ctx** out);
+
+/* As gf_create_batch, but all device storage is carved out of device_buf
+ * (at least gf_footprint bytes, 256-byte aligned, owned by the caller, e.g. a
+ * PyTorch tensor); the context allocates no device memory. */
+int gf_create_ext(const int dims[4], int n_copies, gf_gauge gauge, gf_precision prec, void* stream,
+                  void* device_buf, size_t bytes, gf_ctx** out);
+
+/* Release the context and the device memory it allocated. NULL is ignored. */
+void gf_destroy(gf_ctx* ctx);
+
+/* Load links from host memory (StandardPattern, 72*V doubles) into copy
+ * `copy`, or into every copy when copy = -1.  The first two rows of each
+ * link are kept (12-real storage, Sec. 4.2); the third is rebuilt on use.
+ * For Coulomb the accumulated time-slice gauge transformation is reset. */
+int gf_load_links(gf_ctx* ctx, int copy, const double* host);
+
+/* As gf_load_links for the time-slices [t0, t0+nt) only; host holds
+ * nt*Nx*Ny*Nz*4*18 doubles.  Lets very large lattices stream in slab by slab. */
+int gf_load_links_slab(gf_ctx* ctx, int copy, int t0, int nt, const double* host);
+
+/* As gf_load_links, from device memory in the same natural order. */
+int gf_load_links_device(gf_ctx* ctx, int copy, const double* device_src);
+
+/* Store the links of copy `copy` to host memory (StandardPattern, full 3x3,
+ * third row rebuilt as conj(row0 x row1)).  For Coulomb the accumulated
+ * time-slice transformation is first folded into the temporal links,
+ * U_0(x) <- g(x) U_0(x) g(x+0)^dag (Sec. 5.1). */
+int gf_store_links(gf_ctx* ctx, int copy, double* host);
+
+/* As gf_store_links, to device memory. */
+int gf_store_links_device(gf_ctx* ctx, int copy, double* device_dst);
+
+/* Random gauge transformation U_mu(x) <- g(x) U_mu(x) g(x+mu)^dag with
+ * Haar-random g(x) in SU(3) (a random point on the gauge orbit, Sec. 6.5):
+ * g(x) is drawn from Philox4x32-10 keyed by the seed and counted by (site,
+ * copy), so every copy gets a different transformation. */
+int gf_random_gauge_transform(gf_ctx* ctx, uint64_t seed);
+
+/* n_sweeps checkerboard sweeps (Alg. 1: even sublattice, then odd; per site
+ * the subgroups (0,1), (0,2), (1,2)) over every active unit.  param: omega in
+ * [1,2] for GF_OR (GF_RELAX ignores it and uses 1), the probability p in
+ * [0,1] for GF_SR, the temperature T > 0 for GF_SA, unused for GF_MICRO.
+ * GF_SA: every sweep is one heat-bath sweep followed by three microcanonical
+ * sweeps (Sec. 2.3).  Random draws are keyed by (seed, site, sweep index,
+ * copy); the context's sweep index advances by one per sweep (four per SA
+ * sweep).  F and theta (may be NULL) receive the exact values after the
+ * sweeps, per copy. */
+int gf_sweep(gf_ctx* ctx, gf_algo algo, double param, int n_sweeps, uint64_t seed, double* F,
+             double* theta);
+
+/* Simulated annealing: n_steps heat-bath sweeps with T falling linearly from
+ * T0 to T1, each followed by three microcanonical sweeps (Sec. 2.3). */
+int gf_anneal(gf_ctx* ctx, double T0, double T1, int n_steps, uint64_t seed, double* F, double* theta);
+
+/* Re-unitarise every stored matrix in FP64: normalise row 0, Gram-Schmidt
+ * row 1, normalise; row 2 = conj(row0 x row1) (Sec. 4.5, reprojection). */
+int gf_reunitarize(gf_ctx* ctx);
+
+/* Exact FP64 gauge functional and theta per copy (Sec. 2.1).  Coulomb: the
+ * means over time-slices of F_t and theta_t. */
+int gf_functional_theta(gf_ctx* ctx, double* F, double* theta);
+
+/* Per time-slice F_t and theta_t, arrays of n_copies*Nt (copy-major). */
+int gf_slice_functional_theta(gf_ctx* ctx, double* F_t, double* theta_t);
+
+/* GF_MIXED: switch the storage from FP32 to FP64 (every matrix converted and
+ * re-unitarised in FP64).  No-op when the storage is FP64 already. */
+int gf_promote(gf_ctx* ctx);
+
+/* Mark which units take part in sweeps: n_copies*Nt flags (copy-major, one
+ * per time-slice); NULL makes every unit active.  For Landau and MAG a copy
+ * is swept only if all of its flags are set. */
+int gf_set_active(gf_ctx* ctx, const int* flags);
+
+/* Sweep index used to key the random draws (checkpoint / resume). */
+int gf_get_sweep_index(gf_ctx* ctx, uint64_t* index);
+int gf_set_sweep_index(gf_ctx* ctx, uint64_t index);
+
+/* Philox copy id of the context's copy 0 (default 0): copy k draws with id
+ * base + k, so a lattice fixed alone reproduces its run inside a batch. */
+int gf_set_copy_base(gf_ctx* ctx, uint32_t base);
+
+/* Links per thread of the sweep kernels: 1, 2, 4 or 8 (8/lpt threads share a
+ * site and combine their partial K with warp shuffles); 0 = the tuned
+ * default.  gf_autotune times the four on a scratch copy of the links and
+ * keeps the fastest for each (precision, algorithm) it is asked about. */
+int gf_set_links_per_thread(gf_ctx* ctx, int lpt);
+int gf_get_links_per_thread(gf_ctx* ctx, int* lpt);
+int gf_autotune(gf_ctx* ctx, gf_algo algo, int* best_lpt, double* ms_per_sweep_best);
+
+/* Drive the sweeps to theta < theta_target (the while-loop of Alg. 1).
+ * theta is evaluated every check_interval sweeps; a unit (a copy, or for
+ * Coulomb a copy's time-slice) stops as soon as its theta is below target.
+ * FP32 storage is re-unitarised every reunit_interval sweeps (Sec. 4.5).
+ * GF_MIXED runs FP32 sweeps until every active unit has theta < switch_theta
+ * (or theta stops falling), then promotes to FP64 for the final sweeps. */
+typedef struct {
+  gf_algo algo;          /* GF_OR or GF_RELAX */
+  double param;          /* omega */
+  double theta_target;   /* e.g. 1e-12 */
+  int max_sweeps;        /* per run; GF_ENOTCONV beyond */
+  int check_interval;    /* sweeps between theta evaluations, >= 1 */
+  int reunit_interval;   /* FP32 storage: re-unitarise every this many sweeps (0 = never) */
+  double switch_theta;   /* GF_MIXED: FP32 -> FP64 below this theta (e.g. 1e-8) */
+  uint64_t seed;         /* unused by OR/RELAX; kept for symmetry with gf_sweep */
+} gf_fix_params;
+
+typedef struct {
+  int sweeps;            /* sweeps issued (the slowest unit's count) */
+  int sweeps_fp32;       /* of which in FP32 storage */
+  int sweeps_fp64;       /* of which in FP64 storage */
+  int checks;            /* theta evaluations */
+  int converged;         /* 1 if every unit reached theta_target */
+  double seconds;        /* host wall time of the call */
+  uint64_t site_updates; /* sum over sweeps of the sites actually updated */
+} gf_fix_result;
+
+int gf_fix(gf_ctx* ctx, const gf_fix_params* params, gf_fix_result* result);
+
+/* The device Philox4x32-10 (Salmon et al., SC'11) that keys every random draw
+ * of the sweeps and gauge transformations: out[4k..4k+3] = Philox(counters
+ * [4k..4k+3], key = (seed low word, seed high word)) for k < n.  Host arrays;
+ * the call allocates and frees its own device buffers. */
+int gf_philox(uint64_t seed, const uint32_t* counters, size_t n, uint32_t* out);
+
+/* Geometry and state queries. */
+int gf_get_info(gf_ctx* ctx, int dims[4], int* n_copies, int* gauge, int* precision, int* storage_fp64);
+
+/* Name of a status code, and the calling thread's last error message. */
+const char* gf_strerror(int status);
+const char* gf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GF_H */

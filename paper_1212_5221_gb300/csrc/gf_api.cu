@@ -1,0 +1,836 @@
+// gf_api.cu -- the C ABI of libgf (declared in include/gf.h): context and
+// device-memory management, host<->device layout conversion, the sweep
+// sequencing of Alg. 1 and the convergence driver.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gf.h"
+#include "gf_sweep.cuh"
+#include "gf_launch.h"
+
+using gfk::Geom;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define GF_CUDA(expr)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(GF_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+constexpr size_t ALIGN = 256;
+constexpr size_t STAGING_BYTES = (size_t)256 << 20;
+
+size_t round_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+  size_t links32 = 0, links64 = 0, active = 0, partial = 0, obs = 0, staging = 0, total = 0;
+  int slab_nt = 1;
+};
+
+int check_dims(const int dims[4], int ncopies, int gauge, int prec) {
+  if (!dims) return fail(GF_EINVAL, "dims is NULL");
+  uint64_t V = 1;
+  for (int d = 0; d < 4; ++d) {
+    if (dims[d] < 2 || (dims[d] & 1))
+      return fail(GF_EINVAL, "extent %d of dims is %d: every extent must be even and >= 2", d, dims[d]);
+    V *= (uint64_t)dims[d];
+  }
+  if (V >= (1ull << 31)) return fail(GF_EINVAL, "lattice volume %llu too large (< 2^31)", (unsigned long long)V);
+  if (ncopies < 1) return fail(GF_EINVAL, "n_copies must be >= 1");
+  if ((uint64_t)ncopies * dims[0] * 2 > 65535) return fail(GF_EINVAL, "n_copies * Nt * 2 must be <= 65535");
+  if ((uint64_t)ncopies * V >= (1ull << 40)) return fail(GF_EINVAL, "batch too large");
+  if (gauge < GF_LANDAU || gauge > GF_MAG) return fail(GF_EINVAL, "bad gauge %d", gauge);
+  if (prec < GF_FP64 || prec > GF_MIXED) return fail(GF_EINVAL, "bad precision %d", prec);
+  return GF_OK;
+}
+
+Geom make_geom(const int dims[4]) {
+  Geom G;
+  for (int d = 0; d < 4; ++d) G.n[d] = dims[d];
+  G.V3 = (uint32_t)dims[1] * dims[2] * dims[3];
+  G.V = G.V3 * (uint32_t)dims[0];
+  G.Vh = G.V / 2;
+  G.stride[0] = G.V3;
+  G.stride[1] = (uint32_t)dims[2] * dims[3];
+  G.stride[2] = (uint32_t)dims[3];
+  G.stride[3] = 1;
+  G.dz = gfk::make_fastdiv((uint32_t)dims[3]);
+  G.dy = gfk::make_fastdiv((uint32_t)dims[2]);
+  G.dx = gfk::make_fastdiv((uint32_t)dims[1]);
+  return G;
+}
+
+Layout make_layout(const int dims[4], int ncopies, int gauge, int prec) {
+  Geom G = make_geom(dims);
+  Layout L;
+  const int NS = gauge == GF_COULOMB ? 5 : 4;
+  const size_t mats = (size_t)ncopies * 2 * NS * G.Vh;
+  if (prec != GF_FP64) L.links32 = round_up(mats * 3 * sizeof(float4));
+  if (prec != GF_FP32) L.links64 = round_up(mats * 6 * sizeof(double2));
+  L.active = round_up((size_t)ncopies * dims[0] * sizeof(int));
+  L.partial = round_up(gfk::observables_partial_doubles(G, ncopies) * sizeof(double));
+  L.obs = round_up((size_t)ncopies * dims[0] * 2 * sizeof(double));
+  const size_t slice_bytes = (size_t)G.V3 * 4 * 18 * sizeof(double);
+  L.slab_nt = (int)std::max<size_t>(1, std::min<size_t>(dims[0], STAGING_BYTES / slice_bytes));
+  L.staging = round_up((size_t)L.slab_nt * slice_bytes);
+  L.total = L.links32 + L.links64 + L.active + L.partial + L.obs + L.staging;
+  return L;
+}
+
+}  // namespace
+
+struct gf_ctx {
+  int dims[4];
+  int ncopies, gauge, prec, NS;
+  Geom G;
+  Layout layout;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  void* owned = nullptr;  // device block allocated by the context (nullptr for gf_create_ext)
+  void* links32 = nullptr;
+  void* links64 = nullptr;
+  int* active_d = nullptr;
+  double* partial = nullptr;
+  double* obs_d = nullptr;
+  double* staging = nullptr;
+  bool fp64 = false;  // current storage
+  bool all_active = true;
+  std::vector<int> active_h;
+  uint64_t sweep_index = 0;
+  uint32_t copy_base = 0;  // Philox copy id of copy 0
+  int lpt[2][5] = {{0}};  // [fp64][algo] chosen links per thread, 0 = default
+
+  void* links() const { return fp64 ? links64 : links32; }
+  size_t copy_block_bytes() const {
+    return (size_t)2 * NS * G.Vh * (fp64 ? 6 : 3) * 16;
+  }
+};
+
+namespace {
+
+int default_lpt(const gf_ctx* c, int algo) {
+  int v = c->lpt[c->fp64][algo];
+  if (v) return v;
+  return c->fp64 ? 2 : 1;
+}
+
+int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, uint32_t sweep, int lpt) {
+  cudaError_t e;
+  if (c->fp64) {
+    gfk::SweepArgs<double> a;
+    a.links = static_cast<double2*>(c->links64);
+    a.geom = c->G;
+    a.NS = c->NS;
+    a.parity = parity;
+    a.ncopies = (uint32_t)c->ncopies;
+    a.copy0 = c->copy_base;
+    a.active = c->all_active ? nullptr : c->active_d;
+    a.param = param;
+    a.k0 = (uint32_t)seed;
+    a.k1 = (uint32_t)(seed >> 32);
+    a.sweep = sweep;
+    e = gfk::launch_sweep<double>(a, c->gauge, kalgo, lpt, c->st);
+  } else {
+    gfk::SweepArgs<float> a;
+    a.links = static_cast<float4*>(c->links32);
+    a.geom = c->G;
+    a.NS = c->NS;
+    a.parity = parity;
+    a.ncopies = (uint32_t)c->ncopies;
+    a.copy0 = c->copy_base;
+    a.active = c->all_active ? nullptr : c->active_d;
+    a.param = (float)param;
+    a.k0 = (uint32_t)seed;
+    a.k1 = (uint32_t)(seed >> 32);
+    a.sweep = sweep;
+    e = gfk::launch_sweep<float>(a, c->gauge, kalgo, lpt, c->st);
+  }
+  if (e != cudaSuccess) return fail(GF_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
+  return GF_OK;
+}
+
+// One full sweep (even, then odd sublattice) of kernel algorithm kalgo.
+int full_sweep(gf_ctx* c, int kalgo, int api_algo, double param, uint64_t seed, int lpt_override = 0) {
+  const int lpt = lpt_override ? lpt_override : default_lpt(c, api_algo);
+  const uint32_t sw = (uint32_t)c->sweep_index;
+  for (int p = 0; p < 2; ++p) {
+    int r = launch_half(c, kalgo, param, p, seed, sw, lpt);
+    if (r) return r;
+  }
+  c->sweep_index++;
+  return GF_OK;
+}
+
+int observables(gf_ctx* c, std::vector<double>& per_ct) {
+  cudaError_t e = c->fp64 ? gfk::launch_observables<double>(c->links64, c->G, c->NS, c->gauge, c->ncopies,
+                                                             c->partial, c->obs_d, c->st)
+                          : gfk::launch_observables<float>(c->links32, c->G, c->NS, c->gauge, c->ncopies,
+                                                            c->partial, c->obs_d, c->st);
+  if (e != cudaSuccess) return fail(GF_ECUDA, "observables launch: %s", cudaGetErrorString(e));
+  per_ct.resize((size_t)c->ncopies * c->dims[0] * 2);
+  GF_CUDA(cudaMemcpyAsync(per_ct.data(), c->obs_d, per_ct.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->st));
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  return GF_OK;
+}
+
+void copy_means(const gf_ctx* c, const std::vector<double>& ct, double* F, double* T) {
+  const int Nt = c->dims[0];
+  for (int k = 0; k < c->ncopies; ++k) {
+    double f = 0, t = 0;
+    for (int s = 0; s < Nt; ++s) {
+      f += ct[2 * ((size_t)k * Nt + s)];
+      t += ct[2 * ((size_t)k * Nt + s) + 1];
+    }
+    if (F) F[k] = f / Nt;
+    if (T) T[k] = t / Nt;
+  }
+}
+
+int upload_active(gf_ctx* c) {
+  c->all_active = std::all_of(c->active_h.begin(), c->active_h.end(), [](int v) { return v != 0; });
+  GF_CUDA(cudaMemcpyAsync(c->active_d, c->active_h.data(), c->active_h.size() * sizeof(int),
+                          cudaMemcpyHostToDevice, c->st));
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  return GF_OK;
+}
+
+int coulomb_fold(gf_ctx* c) {
+  if (c->gauge != GF_COULOMB) return GF_OK;
+  cudaError_t e = c->fp64 ? gfk::launch_coulomb_fold<double>(c->links64, c->G, c->ncopies, c->st)
+                          : gfk::launch_coulomb_fold<float>(c->links32, c->G, c->ncopies, c->st);
+  if (e != cudaSuccess) return fail(GF_ECUDA, "coulomb fold: %s", cudaGetErrorString(e));
+  return GF_OK;
+}
+
+int set_identity_slots(gf_ctx* c, int first, int last) {
+  for (int s = first; s <= last; ++s) {
+    cudaError_t e = c->fp64 ? gfk::launch_identity_slot<double>(c->links64, c->G, c->NS, s, c->ncopies, c->st)
+                            : gfk::launch_identity_slot<float>(c->links32, c->G, c->NS, s, c->ncopies, c->st);
+    if (e != cudaSuccess) return fail(GF_ECUDA, "identity: %s", cudaGetErrorString(e));
+  }
+  return GF_OK;
+}
+
+int create_impl(const int dims[4], int ncopies, int gauge, int prec, void* stream, void* buf, size_t bytes,
+                gf_ctx** out) {
+  if (!out) return fail(GF_EINVAL, "out is NULL");
+  *out = nullptr;
+  int r = check_dims(dims, ncopies, gauge, prec);
+  if (r) return r;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(GF_ENOSYS, "no CUDA device available");
+  }
+  gf_ctx* c = new (std::nothrow) gf_ctx;
+  if (!c) return fail(GF_ENOMEM, "host allocation failed");
+  memcpy(c->dims, dims, sizeof c->dims);
+  c->ncopies = ncopies;
+  c->gauge = gauge;
+  c->prec = prec;
+  c->NS = gauge == GF_COULOMB ? 5 : 4;
+  c->G = make_geom(dims);
+  c->layout = make_layout(dims, ncopies, gauge, prec);
+  c->fp64 = prec == GF_FP64;
+  c->active_h.assign((size_t)ncopies * dims[0], 1);
+  if (stream) {
+    c->st = static_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return fail(GF_ECUDA, "cudaStreamCreate failed");
+    }
+    c->own_stream = true;
+  }
+  char* base;
+  if (buf) {
+    if (((uintptr_t)buf % ALIGN) != 0) {
+      gf_destroy(c);
+      return fail(GF_EINVAL, "device_buf must be 256-byte aligned");
+    }
+    if (bytes < c->layout.total) {
+      gf_destroy(c);
+      return fail(GF_ENOMEM, "device_buf has %zu bytes, %zu needed", bytes, c->layout.total);
+    }
+    base = static_cast<char*>(buf);
+  } else {
+    if (cudaMalloc(&c->owned, c->layout.total) != cudaSuccess) {
+      cudaGetLastError();
+      c->owned = nullptr;
+      size_t need = c->layout.total;
+      gf_destroy(c);
+      return fail(GF_ENOMEM, "cudaMalloc of %zu bytes failed", need);
+    }
+    base = static_cast<char*>(c->owned);
+  }
+  const Layout& L = c->layout;
+  size_t off = 0;
+  if (L.links32) { c->links32 = base + off; off += L.links32; }
+  if (L.links64) { c->links64 = base + off; off += L.links64; }
+  c->active_d = reinterpret_cast<int*>(base + off); off += L.active;
+  c->partial = reinterpret_cast<double*>(base + off); off += L.partial;
+  c->obs_d = reinterpret_cast<double*>(base + off); off += L.obs;
+  c->staging = reinterpret_cast<double*>(base + off); off += L.staging;
+  r = upload_active(c);
+  if (!r) r = set_identity_slots(c, 0, c->NS - 1);
+  if (!r) {
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) r = fail(GF_ECUDA, "init: %s", cudaGetErrorString(e));
+  }
+  if (r) {
+    gf_destroy(c);
+    return r;
+  }
+  *out = c;
+  return GF_OK;
+}
+
+int check_ctx(gf_ctx* c) { return c ? GF_OK : fail(GF_EINVAL, "context is NULL"); }
+
+int check_copy(gf_ctx* c, int copy, bool allow_all) {
+  if (copy == -1 && allow_all) return GF_OK;
+  if (copy < 0 || copy >= c->ncopies) return fail(GF_EINVAL, "copy %d out of range [0,%d)", copy, c->ncopies);
+  return GF_OK;
+}
+
+// Import time-slices [t0, t0+nt) of copy `copy` from natural-order doubles on the device.
+int import_slab(gf_ctx* c, int copy, int t0, int nt, const double* dev) {
+  cudaError_t e = c->fp64 ? gfk::launch_import<double>(dev, c->links64, c->G, c->NS, copy, t0, nt, c->st)
+                          : gfk::launch_import<float>(dev, c->links32, c->G, c->NS, copy, t0, nt, c->st);
+  if (e != cudaSuccess) return fail(GF_ECUDA, "import: %s", cudaGetErrorString(e));
+  return GF_OK;
+}
+
+int export_slab(gf_ctx* c, int copy, int t0, int nt, double* dev) {
+  cudaError_t e = c->fp64 ? gfk::launch_export<double>(dev, c->links64, c->G, c->NS, copy, t0, nt, c->st)
+                          : gfk::launch_export<float>(dev, c->links32, c->G, c->NS, copy, t0, nt, c->st);
+  if (e != cudaSuccess) return fail(GF_ECUDA, "export: %s", cudaGetErrorString(e));
+  return GF_OK;
+}
+
+// A new problem: MIXED returns to FP32 storage; Coulomb's accumulated g = 1.
+int begin_load(gf_ctx* c) {
+  if (c->prec == GF_MIXED) c->fp64 = false;
+  if (c->gauge == GF_COULOMB) return set_identity_slots(c, 4, 4);
+  return GF_OK;
+}
+
+int replicate_copy0(gf_ctx* c) {
+  const size_t blk = c->copy_block_bytes();
+  char* base = static_cast<char*>(c->links());
+  for (int k = 1; k < c->ncopies; ++k)
+    GF_CUDA(cudaMemcpyAsync(base + k * blk, base, blk, cudaMemcpyDeviceToDevice, c->st));
+  return GF_OK;
+}
+
+int check_algo_param(int algo, double param) {
+  switch (algo) {
+    case GF_RELAX:
+    case GF_MICRO:
+      return GF_OK;
+    case GF_OR:
+      if (!(param >= 1.0 && param <= 2.0)) return fail(GF_EINVAL, "omega = %g not in [1,2]", param);
+      return GF_OK;
+    case GF_SR:
+      if (!(param >= 0.0 && param <= 1.0)) return fail(GF_EINVAL, "p = %g not in [0,1]", param);
+      return GF_OK;
+    case GF_SA:
+      if (!(param > 0.0) || !std::isfinite(param)) return fail(GF_EINVAL, "T = %g must be > 0", param);
+      return GF_OK;
+  }
+  return fail(GF_EINVAL, "bad algorithm %d", algo);
+}
+
+// One API-level sweep: SA = heat bath + 3 microcanonical sweeps.
+int api_sweep(gf_ctx* c, int algo, double param, uint64_t seed) {
+  switch (algo) {
+    case GF_RELAX: return full_sweep(c, gfk::ALG_OR, GF_RELAX, 1.0, seed);
+    case GF_OR: return full_sweep(c, gfk::ALG_OR, GF_OR, param, seed);
+    case GF_MICRO: return full_sweep(c, gfk::ALG_MICRO, GF_MICRO, 0.0, seed);
+    case GF_SR: return full_sweep(c, gfk::ALG_SR, GF_SR, param, seed);
+    case GF_SA: {
+      int r = full_sweep(c, gfk::ALG_SA, GF_SA, param, seed);
+      for (int k = 0; k < 3 && !r; ++k) r = full_sweep(c, gfk::ALG_MICRO, GF_MICRO, 0.0, seed);
+      return r;
+    }
+  }
+  return fail(GF_EINVAL, "bad algorithm %d", algo);
+}
+
+int reunitarize(gf_ctx* c) {
+  const uint64_t nmat = (uint64_t)c->ncopies * 2 * c->NS * c->G.Vh;
+  cudaError_t e = c->fp64 ? gfk::launch_reunitarize<double>(c->links64, c->G.Vh, nmat, c->st)
+                          : gfk::launch_reunitarize<float>(c->links32, c->G.Vh, nmat, c->st);
+  if (e != cudaSuccess) return fail(GF_ECUDA, "reunitarize: %s", cudaGetErrorString(e));
+  return GF_OK;
+}
+
+int promote(gf_ctx* c) {
+  if (c->fp64) return GF_OK;
+  if (c->prec != GF_MIXED) return fail(GF_EINVAL, "gf_promote needs a GF_MIXED context");
+  const uint64_t nmat = (uint64_t)c->ncopies * 2 * c->NS * c->G.Vh;
+  cudaError_t e = gfk::launch_promote(c->links32, c->links64, c->G.Vh, nmat, c->st);
+  if (e != cudaSuccess) return fail(GF_ECUDA, "promote: %s", cudaGetErrorString(e));
+  c->fp64 = true;
+  return GF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gf_footprint(const int dims[4], int n_copies, gf_gauge gauge, gf_precision prec, size_t* bytes) {
+  int r = check_dims(dims, n_copies, gauge, prec);
+  if (r) return r;
+  if (!bytes) return fail(GF_EINVAL, "bytes is NULL");
+  *bytes = make_layout(dims, n_copies, gauge, prec).total;
+  return GF_OK;
+}
+
+int gf_create(const int dims[4], gf_gauge gauge, gf_precision prec, void* stream, gf_ctx** out) {
+  return create_impl(dims, 1, gauge, prec, stream, nullptr, 0, out);
+}
+
+int gf_create_batch(const int dims[4], int n_copies, gf_gauge gauge, gf_precision prec, void* stream,
+                    gf_ctx** out) {
+  return create_impl(dims, n_copies, gauge, prec, stream, nullptr, 0, out);
+}
+
+int gf_create_ext(const int dims[4], int n_copies, gf_gauge gauge, gf_precision prec, void* stream,
+                  void* device_buf, size_t bytes, gf_ctx** out) {
+  if (!device_buf) return fail(GF_EINVAL, "device_buf is NULL");
+  return create_impl(dims, n_copies, gauge, prec, stream, device_buf, bytes, out);
+}
+
+void gf_destroy(gf_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  if (c->owned) cudaFree(c->owned);
+  if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+  delete c;
+}
+
+int gf_load_links_slab(gf_ctx* c, int copy, int t0, int nt, const double* host) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if ((r = check_copy(c, copy, true))) return r;
+  if (!host) return fail(GF_EINVAL, "host is NULL");
+  if (t0 < 0 || nt < 1 || t0 + nt > c->dims[0]) return fail(GF_EINVAL, "slab [%d,%d) outside [0,%d)", t0, t0 + nt, c->dims[0]);
+  if (t0 == 0 && nt == c->dims[0] && (r = begin_load(c))) return r;
+  const int dst = copy < 0 ? 0 : copy;
+  const size_t per_t = (size_t)c->G.V3 * 4 * 18;
+  for (int t = t0; t < t0 + nt; t += c->layout.slab_nt) {
+    const int n = std::min(c->layout.slab_nt, t0 + nt - t);
+    GF_CUDA(cudaMemcpyAsync(c->staging, host + (size_t)(t - t0) * per_t, (size_t)n * per_t * sizeof(double),
+                            cudaMemcpyHostToDevice, c->st));
+    if ((r = import_slab(c, dst, t, n, c->staging))) return r;
+  }
+  if (copy < 0 && (r = replicate_copy0(c))) return r;
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  return GF_OK;
+}
+
+int gf_load_links(gf_ctx* c, int copy, const double* host) {
+  int r = check_ctx(c);
+  if (r) return r;
+  return gf_load_links_slab(c, copy, 0, c->dims[0], host);
+}
+
+int gf_load_links_device(gf_ctx* c, int copy, const double* dev) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if ((r = check_copy(c, copy, true))) return r;
+  if (!dev) return fail(GF_EINVAL, "device_src is NULL");
+  if ((r = begin_load(c))) return r;
+  if ((r = import_slab(c, copy < 0 ? 0 : copy, 0, c->dims[0], dev))) return r;
+  if (copy < 0 && (r = replicate_copy0(c))) return r;
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  return GF_OK;
+}
+
+int gf_store_links(gf_ctx* c, int copy, double* host) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if ((r = check_copy(c, copy, false))) return r;
+  if (!host) return fail(GF_EINVAL, "host is NULL");
+  if ((r = coulomb_fold(c))) return r;
+  const size_t per_t = (size_t)c->G.V3 * 4 * 18;
+  for (int t = 0; t < c->dims[0]; t += c->layout.slab_nt) {
+    const int n = std::min(c->layout.slab_nt, c->dims[0] - t);
+    if ((r = export_slab(c, copy, t, n, c->staging))) return r;
+    GF_CUDA(cudaMemcpyAsync(host + (size_t)t * per_t, c->staging, (size_t)n * per_t * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->st));
+  }
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  return GF_OK;
+}
+
+int gf_store_links_device(gf_ctx* c, int copy, double* dev) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if ((r = check_copy(c, copy, false))) return r;
+  if (!dev) return fail(GF_EINVAL, "device_dst is NULL");
+  if ((r = coulomb_fold(c))) return r;
+  if ((r = export_slab(c, copy, 0, c->dims[0], dev))) return r;
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  return GF_OK;
+}
+
+int gf_random_gauge_transform(gf_ctx* c, uint64_t seed) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if ((r = coulomb_fold(c))) return r;
+  cudaError_t e = c->fp64 ? gfk::launch_haar_transform<double>(c->links64, c->G, c->NS, c->ncopies, c->copy_base, seed, c->st)
+                          : gfk::launch_haar_transform<float>(c->links32, c->G, c->NS, c->ncopies, c->copy_base, seed, c->st);
+  if (e != cudaSuccess) return fail(GF_ECUDA, "random gauge transform: %s", cudaGetErrorString(e));
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  return GF_OK;
+}
+
+int gf_sweep(gf_ctx* c, gf_algo algo, double param, int n_sweeps, uint64_t seed, double* F, double* theta) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if ((r = check_algo_param(algo, param))) return r;
+  if (n_sweeps < 0) return fail(GF_EINVAL, "n_sweeps < 0");
+  for (int k = 0; k < n_sweeps; ++k)
+    if ((r = api_sweep(c, algo, param, seed))) return r;
+  if (F || theta) {
+    std::vector<double> ct;
+    if ((r = observables(c, ct))) return r;
+    copy_means(c, ct, F, theta);
+  } else {
+    GF_CUDA(cudaStreamSynchronize(c->st));
+  }
+  return GF_OK;
+}
+
+int gf_anneal(gf_ctx* c, double T0, double T1, int n_steps, uint64_t seed, double* F, double* theta) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!(T0 > 0) || !(T1 > 0) || !std::isfinite(T0) || !std::isfinite(T1))
+    return fail(GF_EINVAL, "temperatures must be > 0");
+  if (n_steps < 0) return fail(GF_EINVAL, "n_steps < 0");
+  for (int k = 0; k < n_steps; ++k) {
+    const double T = n_steps > 1 ? T0 + (T1 - T0) * (double)k / (double)(n_steps - 1) : T0;
+    if ((r = api_sweep(c, GF_SA, T, seed))) return r;
+  }
+  if (F || theta) {
+    std::vector<double> ct;
+    if ((r = observables(c, ct))) return r;
+    copy_means(c, ct, F, theta);
+  } else {
+    GF_CUDA(cudaStreamSynchronize(c->st));
+  }
+  return GF_OK;
+}
+
+int gf_reunitarize(gf_ctx* c) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if ((r = reunitarize(c))) return r;
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  return GF_OK;
+}
+
+int gf_functional_theta(gf_ctx* c, double* F, double* theta) {
+  int r = check_ctx(c);
+  if (r) return r;
+  std::vector<double> ct;
+  if ((r = observables(c, ct))) return r;
+  copy_means(c, ct, F, theta);
+  return GF_OK;
+}
+
+int gf_slice_functional_theta(gf_ctx* c, double* F_t, double* theta_t) {
+  int r = check_ctx(c);
+  if (r) return r;
+  std::vector<double> ct;
+  if ((r = observables(c, ct))) return r;
+  for (size_t k = 0; k < ct.size() / 2; ++k) {
+    if (F_t) F_t[k] = ct[2 * k];
+    if (theta_t) theta_t[k] = ct[2 * k + 1];
+  }
+  return GF_OK;
+}
+
+int gf_promote(gf_ctx* c) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if ((r = promote(c))) return r;
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  return GF_OK;
+}
+
+int gf_set_active(gf_ctx* c, const int* flags) {
+  int r = check_ctx(c);
+  if (r) return r;
+  const int Nt = c->dims[0];
+  for (int k = 0; k < c->ncopies; ++k) {
+    bool all = true;
+    for (int t = 0; t < Nt; ++t) {
+      const int v = flags ? (flags[(size_t)k * Nt + t] != 0) : 1;
+      c->active_h[(size_t)k * Nt + t] = v;
+      all = all && v;
+    }
+    if (c->gauge != GF_COULOMB && !all)
+      for (int t = 0; t < Nt; ++t) c->active_h[(size_t)k * Nt + t] = 0;
+  }
+  return upload_active(c);
+}
+
+int gf_get_sweep_index(gf_ctx* c, uint64_t* index) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!index) return fail(GF_EINVAL, "index is NULL");
+  *index = c->sweep_index;
+  return GF_OK;
+}
+
+int gf_set_sweep_index(gf_ctx* c, uint64_t index) {
+  int r = check_ctx(c);
+  if (r) return r;
+  c->sweep_index = index;
+  return GF_OK;
+}
+
+int gf_set_copy_base(gf_ctx* c, uint32_t base) {
+  int r = check_ctx(c);
+  if (r) return r;
+  c->copy_base = base;
+  return GF_OK;
+}
+
+int gf_set_links_per_thread(gf_ctx* c, int lpt) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (lpt != 0 && lpt != 1 && lpt != 2 && lpt != 4 && lpt != 8) return fail(GF_EINVAL, "lpt must be 0,1,2,4,8");
+  for (int p = 0; p < 2; ++p)
+    for (int a = 0; a < 5; ++a) c->lpt[p][a] = lpt;
+  return GF_OK;
+}
+
+int gf_get_links_per_thread(gf_ctx* c, int* lpt) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!lpt) return fail(GF_EINVAL, "lpt is NULL");
+  *lpt = default_lpt(c, GF_OR);
+  return GF_OK;
+}
+
+int gf_autotune(gf_ctx* c, gf_algo algo, int* best_lpt, double* ms_best) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (algo < GF_RELAX || algo > GF_SA) return fail(GF_EINVAL, "bad algorithm %d", algo);
+  const size_t bytes = c->copy_block_bytes() * c->ncopies;
+  void* backup = nullptr;
+  if (cudaMalloc(&backup, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GF_ENOMEM, "autotune scratch of %zu bytes", bytes);
+  }
+  GF_CUDA(cudaMemcpyAsync(backup, c->links(), bytes, cudaMemcpyDeviceToDevice, c->st));
+  const uint64_t idx0 = c->sweep_index;
+  const int kalgo = algo == GF_MICRO ? gfk::ALG_MICRO : algo == GF_SR ? gfk::ALG_SR : algo == GF_SA ? gfk::ALG_SA : gfk::ALG_OR;
+  const double param = algo == GF_SR ? 0.5 : algo == GF_SA ? 1.0 : algo == GF_OR ? 1.7 : 1.0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = 0;
+  float best_ms = 1e30f;
+  const int cands[4] = {1, 2, 4, 8};
+  for (int lpt : cands) {
+    r = full_sweep(c, kalgo, algo, param, 1, lpt);  // warm-up
+    if (r) break;
+    const int reps = 3;
+    cudaEventRecord(e0, c->st);
+    for (int k = 0; k < reps && !r; ++k) r = full_sweep(c, kalgo, algo, param, 1, lpt);
+    cudaEventRecord(e1, c->st);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = lpt;
+    }
+    cudaMemcpyAsync(c->links(), backup, bytes, cudaMemcpyDeviceToDevice, c->st);
+  }
+  cudaStreamSynchronize(c->st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(backup);
+  c->sweep_index = idx0;
+  if (r) return r;
+  c->lpt[c->fp64][algo] = best;
+  if (best_lpt) *best_lpt = best;
+  if (ms_best) *ms_best = best_ms;
+  return GF_OK;
+}
+
+int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!P) return fail(GF_EINVAL, "params is NULL");
+  if (P->algo != GF_OR && P->algo != GF_RELAX) return fail(GF_EINVAL, "gf_fix runs GF_OR or GF_RELAX");
+  if ((r = check_algo_param(P->algo, P->param))) return r;
+  if (!(P->theta_target > 0)) return fail(GF_EINVAL, "theta_target must be > 0");
+  if (P->max_sweeps < 0 || P->check_interval < 1 || P->reunit_interval < 0)
+    return fail(GF_EINVAL, "bad sweep counts");
+  const auto t_start = std::chrono::steady_clock::now();
+  gf_fix_result R;
+  memset(&R, 0, sizeof R);
+  const int Nt = c->dims[0];
+  const int units_per_copy = c->gauge == GF_COULOMB ? Nt : 1;
+  const uint64_t sites_per_unit = c->gauge == GF_COULOMB ? c->G.V3 : c->G.V;
+  std::vector<double> ct;
+  std::vector<double> unit_theta((size_t)c->ncopies * units_per_copy);
+  double best_fp32 = INFINITY;
+  int stall = 0;
+  int since_reunit = 0;
+  for (;;) {
+    if ((r = observables(c, ct))) return r;
+    R.checks++;
+    // theta per unit: a copy (Landau/MAG, mean over slices) or a time-slice (Coulomb)
+    double worst = 0;
+    int n_active = 0;
+    for (int k = 0; k < c->ncopies; ++k) {
+      if (c->gauge == GF_COULOMB) {
+        for (int t = 0; t < Nt; ++t) unit_theta[(size_t)k * Nt + t] = ct[2 * ((size_t)k * Nt + t) + 1];
+      } else {
+        double s = 0;
+        for (int t = 0; t < Nt; ++t) s += ct[2 * ((size_t)k * Nt + t) + 1];
+        unit_theta[k] = s / Nt;
+      }
+    }
+    const bool final_phase = c->fp64 || c->prec == GF_FP32;
+    for (int k = 0; k < c->ncopies; ++k)
+      for (int u = 0; u < units_per_copy; ++u) {
+        const double th = unit_theta[(size_t)k * units_per_copy + u];
+        const bool done = final_phase && th < P->theta_target;
+        const int v = done ? 0 : 1;
+        if (c->gauge == GF_COULOMB) {
+          c->active_h[(size_t)k * Nt + u] = v;
+        } else {
+          for (int t = 0; t < Nt; ++t) c->active_h[(size_t)k * Nt + t] = v;
+        }
+        if (v) {
+          n_active++;
+          worst = std::max(worst, th);
+        }
+      }
+    if ((r = upload_active(c))) return r;
+    if (n_active == 0) {
+      R.converged = 1;
+      break;
+    }
+    if (R.sweeps >= P->max_sweeps) break;
+    if (!c->fp64 && c->prec == GF_MIXED) {
+      if (worst < best_fp32 * 0.9) {
+        best_fp32 = worst;
+        stall = 0;
+      } else {
+        stall++;
+      }
+      if (worst < P->switch_theta || stall >= 5 || !std::isfinite(worst)) {
+        if ((r = promote(c))) return r;
+        continue;  // re-evaluate theta in FP64
+      }
+    }
+    const int k = std::min(P->check_interval, P->max_sweeps - R.sweeps);
+    for (int i = 0; i < k; ++i) {
+      if ((r = api_sweep(c, P->algo, P->param, P->seed))) return r;
+      R.site_updates += (uint64_t)n_active * sites_per_unit;
+      if (c->fp64) {
+        R.sweeps_fp64++;
+      } else {
+        R.sweeps_fp32++;
+        if (P->reunit_interval > 0 && ++since_reunit >= P->reunit_interval) {
+          since_reunit = 0;
+          if ((r = reunitarize(c))) return r;
+        }
+      }
+    }
+    R.sweeps += k;
+  }
+  // leave every unit active for later calls
+  std::fill(c->active_h.begin(), c->active_h.end(), 1);
+  if ((r = upload_active(c))) return r;
+  R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  if (res) *res = R;
+  if (!R.converged) return fail(GF_ENOTCONV, "theta_target not reached in %d sweeps", R.sweeps);
+  return GF_OK;
+}
+
+int gf_get_info(gf_ctx* c, int dims[4], int* n_copies, int* gauge, int* precision, int* storage_fp64) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (dims) memcpy(dims, c->dims, sizeof c->dims);
+  if (n_copies) *n_copies = c->ncopies;
+  if (gauge) *gauge = c->gauge;
+  if (precision) *precision = c->prec;
+  if (storage_fp64) *storage_fp64 = c->fp64;
+  return GF_OK;
+}
+
+int gf_philox(uint64_t seed, const uint32_t* counters, size_t n, uint32_t* out) {
+  if (n == 0) return GF_OK;
+  if (!counters || !out) return fail(GF_EINVAL, "NULL array");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(GF_ENOSYS, "no CUDA device available");
+  }
+  void *dc = nullptr, *dout = nullptr;
+  const size_t bytes = n * 4 * sizeof(uint32_t);
+  if (cudaMalloc(&dc, bytes) != cudaSuccess || cudaMalloc(&dout, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(dc);
+    return fail(GF_ENOMEM, "gf_philox: %zu bytes", 2 * bytes);
+  }
+  int r = GF_OK;
+  cudaError_t e = cudaMemcpy(dc, counters, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = gfk::launch_philox(dc, dout, n, seed, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) r = fail(GF_ECUDA, "gf_philox: %s", cudaGetErrorString(e));
+  cudaFree(dc);
+  cudaFree(dout);
+  return r;
+}
+
+const char* gf_strerror(int status) {
+  switch (status) {
+    case GF_OK: return "GF_OK";
+    case GF_EINVAL: return "GF_EINVAL: invalid argument";
+    case GF_ENOMEM: return "GF_ENOMEM: out of device memory";
+    case GF_ECUDA: return "GF_ECUDA: CUDA error";
+    case GF_ETIMEOUT: return "GF_ETIMEOUT: bounded wait expired";
+    case GF_ENOTCONV: return "GF_ENOTCONV: not converged";
+    case GF_ENOSYS: return "GF_ENOSYS: no CUDA device";
+  }
+  return "unknown status";
+}
+
+const char* gf_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,46 @@
+// gf_launch.h -- host-side launchers of the device kernels (internal to libgf).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "gf_device.cuh"
+
+namespace gfk {
+
+template <typename R>
+struct SweepArgs;
+
+// One half-sweep of the given gauge/algorithm with lpt links per thread.
+template <typename R>
+cudaError_t launch_sweep(const SweepArgs<R>& a, int gauge, int algo, int lpt, cudaStream_t st);
+
+// Exact F/theta per (copy, slice) into out[ct][2] (device).
+template <typename R>
+cudaError_t launch_observables(const void* links, const Geom& G, int NS, int gauge, uint32_t ncopies,
+                               double* partial, double* out, cudaStream_t st);
+size_t observables_partial_doubles(const Geom& G, uint32_t ncopies);
+
+template <typename R>
+cudaError_t launch_reunitarize(void* links, uint32_t Vh, uint64_t nmat, cudaStream_t st);
+cudaError_t launch_promote(const void* src32, void* dst64, uint32_t Vh, uint64_t nmat, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_import(const double* nat, void* links, const Geom& G, int NS, uint32_t copy, uint32_t t0,
+                          uint32_t nt, cudaStream_t st);
+template <typename R>
+cudaError_t launch_export(double* nat, const void* links, const Geom& G, int NS, uint32_t copy, uint32_t t0,
+                          uint32_t nt, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_haar_transform(void* links, const Geom& G, int NS, uint32_t ncopies, uint32_t copy0,
+                                  uint64_t seed, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_coulomb_fold(void* links, const Geom& G, uint32_t ncopies, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_identity_slot(void* links, const Geom& G, int NS, int slot, uint32_t ncopies,
+                                 cudaStream_t st);
+
+cudaError_t launch_philox(const void* ctr, void* out, uint64_t n, uint64_t seed, cudaStream_t st);
+
+}  // namespace gfk

@@ -1,0 +1,354 @@
+"""Thin ctypes binding of libgf (include/gf.h): argument marshalling only.
+
+Every function keeps the C name and raises GFError on a non-zero status.
+Link arrays are complex128 numpy arrays of shape (Nt, Nx, Ny, Nz, 4, 3, 3)
+(the natural order of Sec. 4.2.1) or, for the *_device calls, CUDA tensors
+of the same shape.  There is no fallback: if libgf.so is missing or no GPU
+is present, the calls fail loudly.
+
+``GaugeField`` is a small convenience wrapper whose device storage and CUDA
+stream come from PyTorch (gf_create_ext with a torch buffer and torch's
+current stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgf.so")
+
+GF_LANDAU, GF_COULOMB, GF_MAG = 0, 1, 2
+GF_FP64, GF_FP32, GF_MIXED = 0, 1, 2
+GF_RELAX, GF_OR, GF_MICRO, GF_SR, GF_SA = 0, 1, 2, 3, 4
+GF_OK, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_ETIMEOUT, GF_ENOTCONV, GF_ENOSYS = range(7)
+
+GAUGES = {"landau": GF_LANDAU, "coulomb": GF_COULOMB, "mag": GF_MAG}
+PRECISIONS = {"fp64": GF_FP64, "fp32": GF_FP32, "mixed": GF_MIXED}
+ALGOS = {"relax": GF_RELAX, "or": GF_OR, "micro": GF_MICRO, "sr": GF_SR, "sa": GF_SA}
+
+
+class GFError(RuntimeError):
+    def __init__(self, code: int, where: str, message: str):
+        self.code = code
+        super().__init__(f"{where}: status {code} ({message})")
+
+
+class gf_fix_params(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int), ("param", ctypes.c_double), ("theta_target", ctypes.c_double),
+                ("max_sweeps", ctypes.c_int), ("check_interval", ctypes.c_int),
+                ("reunit_interval", ctypes.c_int), ("switch_theta", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+class gf_fix_result(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("sweeps_fp32", ctypes.c_int), ("sweeps_fp64", ctypes.c_int),
+                ("checks", ctypes.c_int), ("converged", ctypes.c_int), ("seconds", ctypes.c_double),
+                ("site_updates", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_PD = ctypes.POINTER(ctypes.c_double)
+_PI = ctypes.POINTER(ctypes.c_int)
+_SIG = {
+    "gf_footprint": [_PI, _I, _I, _I, ctypes.POINTER(ctypes.c_size_t)],
+    "gf_create": [_PI, _I, _I, _P, ctypes.POINTER(_P)],
+    "gf_create_batch": [_PI, _I, _I, _I, _P, ctypes.POINTER(_P)],
+    "gf_create_ext": [_PI, _I, _I, _I, _P, _P, ctypes.c_size_t, ctypes.POINTER(_P)],
+    "gf_load_links": [_P, _I, _P],
+    "gf_load_links_slab": [_P, _I, _I, _I, _P],
+    "gf_load_links_device": [_P, _I, _P],
+    "gf_store_links": [_P, _I, _P],
+    "gf_store_links_device": [_P, _I, _P],
+    "gf_random_gauge_transform": [_P, ctypes.c_uint64],
+    "gf_sweep": [_P, _I, _D, _I, ctypes.c_uint64, _P, _P],
+    "gf_anneal": [_P, _D, _D, _I, ctypes.c_uint64, _P, _P],
+    "gf_reunitarize": [_P],
+    "gf_functional_theta": [_P, _P, _P],
+    "gf_slice_functional_theta": [_P, _P, _P],
+    "gf_promote": [_P],
+    "gf_set_active": [_P, _P],
+    "gf_get_sweep_index": [_P, ctypes.POINTER(ctypes.c_uint64)],
+    "gf_set_sweep_index": [_P, ctypes.c_uint64],
+    "gf_set_copy_base": [_P, ctypes.c_uint32],
+    "gf_set_links_per_thread": [_P, _I],
+    "gf_get_links_per_thread": [_P, _PI],
+    "gf_autotune": [_P, _I, _PI, _PD],
+    "gf_fix": [_P, ctypes.POINTER(gf_fix_params), ctypes.POINTER(gf_fix_result)],
+    "gf_get_info": [_P, _PI, _PI, _PI, _PI, _PI],
+    "gf_philox": [ctypes.c_uint64, _P, ctypes.c_size_t, _P],
+}
+_lib = None
+
+
+def lib():
+    """Load libgf.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_1212_5221_gb300.build.build_all()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIG.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = _I
+        L.gf_destroy.argtypes = [_P]
+        L.gf_destroy.restype = None
+        L.gf_strerror.argtypes = [_I]
+        L.gf_strerror.restype = ctypes.c_char_p
+        L.gf_last_error.argtypes = []
+        L.gf_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != GF_OK:
+        msg = lib().gf_last_error().decode()
+        raise GFError(status, where, msg or lib().gf_strerror(status).decode())
+
+
+def _dims(dims):
+    dims = tuple(int(d) for d in dims)
+    if len(dims) != 4:
+        raise ValueError("dims must be (Nt, Nx, Ny, Nz)")
+    return (ctypes.c_int * 4)(*dims)
+
+
+def _enum(v, table):
+    return table[v] if isinstance(v, str) else int(v)
+
+
+def _links_arg(U, dims_nt=None):
+    if not isinstance(U, np.ndarray) or U.dtype != np.complex128 or not U.flags.c_contiguous:
+        raise ValueError("links must be a C-contiguous complex128 numpy array")
+    return U.ctypes.data
+
+
+def gf_strerror(status: int) -> str:
+    return lib().gf_strerror(status).decode()
+
+
+def gf_last_error() -> str:
+    return lib().gf_last_error().decode()
+
+
+def gf_footprint(dims, n_copies=1, gauge="landau", prec="fp64") -> int:
+    out = ctypes.c_size_t()
+    _check(lib().gf_footprint(_dims(dims), n_copies, _enum(gauge, GAUGES), _enum(prec, PRECISIONS),
+                              ctypes.byref(out)), "gf_footprint")
+    return out.value
+
+
+def gf_create(dims, gauge="landau", prec="fp64", stream=None):
+    h = _P()
+    _check(lib().gf_create(_dims(dims), _enum(gauge, GAUGES), _enum(prec, PRECISIONS), stream,
+                           ctypes.byref(h)), "gf_create")
+    return h
+
+
+def gf_create_batch(dims, n_copies, gauge="landau", prec="fp64", stream=None):
+    h = _P()
+    _check(lib().gf_create_batch(_dims(dims), n_copies, _enum(gauge, GAUGES), _enum(prec, PRECISIONS), stream,
+                                 ctypes.byref(h)), "gf_create_batch")
+    return h
+
+
+def gf_create_ext(dims, n_copies, gauge, prec, stream, device_ptr: int, nbytes: int):
+    h = _P()
+    _check(lib().gf_create_ext(_dims(dims), n_copies, _enum(gauge, GAUGES), _enum(prec, PRECISIONS), stream,
+                               _P(device_ptr), nbytes, ctypes.byref(h)), "gf_create_ext")
+    return h
+
+
+def gf_destroy(h):
+    if h:
+        lib().gf_destroy(h)
+
+
+def gf_load_links(h, copy, U):
+    _check(lib().gf_load_links(h, copy, _links_arg(U)), "gf_load_links")
+
+
+def gf_load_links_slab(h, copy, t0, nt, U):
+    _check(lib().gf_load_links_slab(h, copy, t0, nt, _links_arg(U)), "gf_load_links_slab")
+
+
+def gf_load_links_device(h, copy, dev_ptr: int):
+    _check(lib().gf_load_links_device(h, copy, _P(dev_ptr)), "gf_load_links_device")
+
+
+def gf_store_links(h, copy, out):
+    _check(lib().gf_store_links(h, copy, _links_arg(out)), "gf_store_links")
+
+
+def gf_store_links_device(h, copy, dev_ptr: int):
+    _check(lib().gf_store_links_device(h, copy, _P(dev_ptr)), "gf_store_links_device")
+
+
+def gf_random_gauge_transform(h, seed):
+    _check(lib().gf_random_gauge_transform(h, int(seed) & (2**64 - 1)), "gf_random_gauge_transform")
+
+
+def _ncopies(h):
+    n = ctypes.c_int()
+    _check(lib().gf_get_info(h, None, ctypes.byref(n), None, None, None), "gf_get_info")
+    return n.value
+
+
+def gf_sweep(h, algo, param=1.0, n_sweeps=1, seed=0, observables=True):
+    n = _ncopies(h)
+    F = np.zeros(n)
+    T = np.zeros(n)
+    _check(lib().gf_sweep(h, _enum(algo, ALGOS), float(param), int(n_sweeps), int(seed) & (2**64 - 1),
+                          F.ctypes.data if observables else None, T.ctypes.data if observables else None),
+           "gf_sweep")
+    return (F, T) if observables else None
+
+
+def gf_anneal(h, T0, T1, n_steps, seed=0, observables=True):
+    n = _ncopies(h)
+    F = np.zeros(n)
+    T = np.zeros(n)
+    _check(lib().gf_anneal(h, float(T0), float(T1), int(n_steps), int(seed) & (2**64 - 1),
+                           F.ctypes.data if observables else None, T.ctypes.data if observables else None),
+           "gf_anneal")
+    return (F, T) if observables else None
+
+
+def gf_reunitarize(h):
+    _check(lib().gf_reunitarize(h), "gf_reunitarize")
+
+
+def gf_functional_theta(h):
+    n = _ncopies(h)
+    F = np.zeros(n)
+    T = np.zeros(n)
+    _check(lib().gf_functional_theta(h, F.ctypes.data, T.ctypes.data), "gf_functional_theta")
+    return F, T
+
+
+def gf_slice_functional_theta(h):
+    dims = (ctypes.c_int * 4)()
+    n = ctypes.c_int()
+    _check(lib().gf_get_info(h, dims, ctypes.byref(n), None, None, None), "gf_get_info")
+    F = np.zeros((n.value, dims[0]))
+    T = np.zeros((n.value, dims[0]))
+    _check(lib().gf_slice_functional_theta(h, F.ctypes.data, T.ctypes.data), "gf_slice_functional_theta")
+    return F, T
+
+
+def gf_promote(h):
+    _check(lib().gf_promote(h), "gf_promote")
+
+
+def gf_set_active(h, flags=None):
+    arr = None if flags is None else np.ascontiguousarray(flags, dtype=np.int32)
+    _check(lib().gf_set_active(h, None if arr is None else arr.ctypes.data), "gf_set_active")
+
+
+def gf_get_sweep_index(h):
+    v = ctypes.c_uint64()
+    _check(lib().gf_get_sweep_index(h, ctypes.byref(v)), "gf_get_sweep_index")
+    return v.value
+
+
+def gf_set_sweep_index(h, index):
+    _check(lib().gf_set_sweep_index(h, int(index)), "gf_set_sweep_index")
+
+
+def gf_set_copy_base(h, base):
+    _check(lib().gf_set_copy_base(h, int(base)), "gf_set_copy_base")
+
+
+def gf_set_links_per_thread(h, lpt):
+    _check(lib().gf_set_links_per_thread(h, int(lpt)), "gf_set_links_per_thread")
+
+
+def gf_get_links_per_thread(h):
+    v = ctypes.c_int()
+    _check(lib().gf_get_links_per_thread(h, ctypes.byref(v)), "gf_get_links_per_thread")
+    return v.value
+
+
+def gf_autotune(h, algo="or"):
+    best = ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(lib().gf_autotune(h, _enum(algo, ALGOS), ctypes.byref(best), ctypes.byref(ms)), "gf_autotune")
+    return best.value, ms.value
+
+
+def gf_fix(h, algo="or", param=1.7, theta_target=1e-12, max_sweeps=100000, check_interval=10,
+           reunit_interval=100, switch_theta=1e-8, seed=0, raise_on_notconv=True):
+    p = gf_fix_params(_enum(algo, ALGOS), float(param), float(theta_target), int(max_sweeps),
+                      int(check_interval), int(reunit_interval), float(switch_theta), int(seed))
+    r = gf_fix_result()
+    st = lib().gf_fix(h, ctypes.byref(p), ctypes.byref(r))
+    if st == GF_ENOTCONV and not raise_on_notconv:
+        return r.as_dict()
+    _check(st, "gf_fix")
+    return r.as_dict()
+
+
+def gf_get_info(h):
+    dims = (ctypes.c_int * 4)()
+    n, g, p, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().gf_get_info(h, dims, ctypes.byref(n), ctypes.byref(g), ctypes.byref(p), ctypes.byref(f)),
+           "gf_get_info")
+    return dict(dims=tuple(dims), n_copies=n.value, gauge=g.value, precision=p.value, storage_fp64=bool(f.value))
+
+
+def gf_philox(seed, counters):
+    """Device Philox4x32-10 of an (n, 4) uint32 array of counters."""
+    c = np.ascontiguousarray(counters, dtype=np.uint32)
+    if c.ndim != 2 or c.shape[1] != 4:
+        raise ValueError("counters must have shape (n, 4)")
+    out = np.empty_like(c)
+    _check(lib().gf_philox(int(seed) & (2**64 - 1), c.ctypes.data, c.shape[0], out.ctypes.data), "gf_philox")
+    return out
+
+
+class GaugeField:
+    """A context whose device memory and stream are PyTorch's.
+
+    The buffer is a torch uint8 CUDA tensor of gf_footprint bytes and work is
+    issued on a torch.cuda.Stream created for the field (or the one given).
+    """
+
+    def __init__(self, dims, gauge="landau", prec="fp64", n_copies=1, device=None, stream=None):
+        import torch
+
+        self.dims = tuple(int(d) for d in dims)
+        self.n_copies = int(n_copies)
+        nbytes = gf_footprint(self.dims, self.n_copies, gauge, prec)
+        dev = torch.device("cuda" if device is None else device)
+        self.buffer = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        ptr = self.buffer.data_ptr()
+        aligned = (ptr + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.Stream(dev)
+        self.h = gf_create_ext(self.dims, self.n_copies, gauge, prec, _P(self.stream.cuda_stream), aligned,
+                               nbytes + 256 - (aligned - ptr))
+
+    def close(self):
+        if getattr(self, "h", None):
+            gf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

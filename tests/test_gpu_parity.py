@@ -1,0 +1,355 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle.
+
+Tolerances: FP64 storage max|dU| <= 1e-12 per sweep, FP32 storage
+max|dU| <= 2e-5 (the precision acceptance of Sec. 4.5); observables
+relative 1e-12 (FP64) / 1e-5 (FP32); converged functionals 1e-9 relative
+at theta < 1e-12.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 2e-5}
+GAUGES = ["landau", "coulomb", "mag"]
+# several blocks and a ragged tail for every links-per-thread choice
+DIMS = (6, 4, 6, 10)
+
+
+@pytest.fixture(scope="module")
+def gf():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1212_5221_gb300 import build, gf
+
+    build.build_lib()
+    return gf
+
+
+class Ctx:
+    def __init__(self, gf, dims, gauge, prec, n_copies=1):
+        self.gf = gf
+        self.h = gf.gf_create_batch(dims, n_copies, gauge, prec)
+        self.dims = dims
+
+    def __enter__(self):
+        return self.h
+
+    def __exit__(self, *a):
+        self.gf.gf_destroy(self.h)
+
+
+def rough(synth, orc, dims, eps=0.4, seed=3, gseed=11):
+    U = synth.links(dims, "smooth", eps, seed)
+    orc.random_gauge_transform(U, gseed)
+    return U
+
+
+def store(gf, h, dims, copy=0):
+    out = np.empty(tuple(dims) + (4, 3, 3), np.complex128)
+    gf.gf_store_links(h, copy, out)
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_load_store_roundtrip(gf, synth, orc, prec):
+    U = rough(synth, orc, DIMS)
+    with Ctx(gf, DIMS, "landau", prec) as h:
+        gf.gf_load_links(h, 0, U)
+        V = store(gf, h, DIMS)
+    assert np.abs(V - U).max() < (1e-14 if prec == "fp64" else 3e-7)
+
+
+def test_philox_bit_identical(gf, orc):
+    rng = np.random.default_rng(5)
+    n = 1 << 20
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    seed = 0x1234_5678_9ABC_DEF0
+    out = gf.gf_philox(seed, ctr)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for k in rng.integers(0, n, 2000):
+        assert tuple(int(v) for v in out[k]) == orc.philox4x32_10(ctr[k], key)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("gauge", GAUGES)
+def test_observables(gf, synth, orc, gauge, prec):
+    U = rough(synth, orc, DIMS)
+    F, th, Ft, tht = orc.observables(U, gauge)
+    with Ctx(gf, DIMS, gauge, prec) as h:
+        gf.gf_load_links(h, 0, U)
+        gF, gT = gf.gf_functional_theta(h)
+        sF, sT = gf.gf_slice_functional_theta(h)
+    rtol = 1e-12 if prec == "fp64" else 1e-5
+    assert abs(gF[0] - F) <= rtol * abs(F)
+    assert abs(gT[0] - th) <= rtol * abs(th)
+    assert np.allclose(sF[0], Ft, rtol=rtol, atol=0)
+    assert np.allclose(sT[0], tht, rtol=rtol, atol=0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_random_gauge_transform(gf, synth, orc, prec):
+    U = synth.links(DIMS, "smooth", 0.4, 3)
+    with Ctx(gf, DIMS, "landau", prec, n_copies=2) as h:
+        gf.gf_load_links(h, -1, U)
+        gf.gf_random_gauge_transform(h, 1234)
+        V0 = store(gf, h, DIMS, 0)
+        V1 = store(gf, h, DIMS, 1)
+    W0, W1 = U.copy(), U.copy()
+    orc.random_gauge_transform(W0, 1234, 0)
+    orc.random_gauge_transform(W1, 1234, 1)
+    assert np.abs(V0 - W0).max() <= TOL[prec]
+    assert np.abs(V1 - W1).max() <= TOL[prec]
+    assert np.abs(W0 - W1).max() > 0.1  # copies get different transformations
+
+
+@pytest.mark.parametrize("lpt", [1, 2, 4, 8])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("algo,param", [("relax", 1.0), ("or", 1.7), ("micro", 0.0), ("sr", 0.5)])
+@pytest.mark.parametrize("gauge", GAUGES)
+def test_single_sweep(gf, synth, orc, gauge, algo, param, prec, lpt):
+    U = rough(synth, orc, DIMS, 0.5, 4, 12)
+    W = U.copy()
+    orc.sweep(W, gauge, algo, param, 1, 0, 99)
+    with Ctx(gf, DIMS, gauge, prec) as h:
+        gf.gf_set_links_per_thread(h, lpt)
+        gf.gf_load_links(h, 0, U)
+        gf.gf_sweep(h, algo, param, 1, 99, observables=False)
+        V = store(gf, h, DIMS)
+    err = np.abs(V - W).max()
+    assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("lpt", [1, 8])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("gauge", GAUGES)
+def test_single_sa_sweep(gf, synth, orc, gauge, prec, lpt):
+    """Heat bath + three microcanonical sweeps with identical Philox draws.
+
+    Where floating point decides an accept/reject branch, the two sides may
+    take different branches for draws within rounding of a threshold: FP64
+    must agree everywhere; FP32 may differ on a tiny fraction of links."""
+    T = 1.5
+    U = rough(synth, orc, DIMS, 0.5, 4, 12)
+    W = U.copy()
+    orc.sweep(W, gauge, "sa", T, 1, 0, 7)
+    orc.sweep(W, gauge, "micro", 0.0, 3, 1, 7)
+    with Ctx(gf, DIMS, gauge, prec) as h:
+        gf.gf_set_links_per_thread(h, lpt)
+        gf.gf_load_links(h, 0, U)
+        gf.gf_sweep(h, "sa", T, 1, 7, observables=False)
+        assert gf.gf_get_sweep_index(h) == 4
+        V = store(gf, h, DIMS)
+    d = np.abs(V - W).reshape(-1, 9).max(1)
+    if prec == "fp64":
+        assert d.max() <= 1e-11
+    else:
+        bad = (d > 2e-4).mean()
+        assert bad <= 0.01, bad
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("gauge", GAUGES)
+def test_ten_sweeps_and_observables(gf, synth, orc, gauge, prec):
+    U = rough(synth, orc, DIMS, 0.4, 5, 13)
+    W = U.copy()
+    orc.sweep(W, gauge, "or", 1.7, 10)
+    F, th, _, _ = orc.observables(W, gauge)
+    with Ctx(gf, DIMS, gauge, prec) as h:
+        gf.gf_load_links(h, 0, U)
+        gF, gT = gf.gf_sweep(h, "or", 1.7, 10)
+        V = store(gf, h, DIMS)
+    assert np.abs(V - W).max() <= (1e-11 if prec == "fp64" else 2e-4)
+    assert abs(gF[0] - F) <= (1e-12 if prec == "fp64" else 1e-5) * abs(F)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_reunitarize(gf, synth, orc, prec):
+    U = rough(synth, orc, DIMS)
+    rng = np.random.default_rng(1)
+    U = U + 1e-4 * (rng.normal(size=U.shape) + 1j * rng.normal(size=U.shape))
+    W = U.copy()
+    orc.reunitarize(W)
+    with Ctx(gf, DIMS, "landau", prec) as h:
+        gf.gf_load_links(h, 0, U)
+        gf.gf_reunitarize(h)
+        V = store(gf, h, DIMS)
+    assert np.abs(V - W).max() <= (1e-14 if prec == "fp64" else 3e-7)
+
+
+def test_promote(gf, synth, orc):
+    U = rough(synth, orc, DIMS)
+    with Ctx(gf, DIMS, "landau", "mixed") as h:
+        gf.gf_load_links(h, 0, U)
+        assert not gf.gf_get_info(h)["storage_fp64"]
+        gf.gf_promote(h)
+        assert gf.gf_get_info(h)["storage_fp64"]
+        V = store(gf, h, DIMS)
+    M = V.reshape(-1, 3, 3)
+    assert np.abs(M @ M.conj().transpose(0, 2, 1) - np.eye(3)).max() < 1e-14
+    assert np.abs(V - U).max() < 3e-7
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_coulomb_fold(gf, synth, orc, prec):
+    """Time-slice sweeps with the accumulated g, folded into U_0 on store,
+    equal the oracle's in-place sweeps of all four directions."""
+    U = rough(synth, orc, DIMS, 0.4, 2, 9)
+    W = U.copy()
+    orc.sweep(W, "coulomb", "or", 1.7, 6)
+    with Ctx(gf, DIMS, "coulomb", prec) as h:
+        gf.gf_load_links(h, 0, U)
+        gf.gf_sweep(h, "or", 1.7, 6, observables=False)
+        V = store(gf, h, DIMS)
+        V2 = store(gf, h, DIMS)  # folding twice changes nothing
+    assert np.abs(V - W).max() <= (1e-11 if prec == "fp64" else 2e-4)
+    assert np.abs(V2 - V).max() <= (1e-15 if prec == "fp64" else 1e-6)
+    assert abs(orc.plaquette(V) - orc.plaquette(U)) < (1e-12 if prec == "fp64" else 1e-5)
+
+
+def test_fix_unit_field(gf, synth, orc):
+    dims = (8, 8, 8, 8)
+    U = synth.links(dims, "unit")
+    with Ctx(gf, dims, "landau", "fp64") as h:
+        gf.gf_load_links(h, 0, U)
+        gf.gf_random_gauge_transform(h, 5)
+        r = gf.gf_fix(h, "or", 1.7, 1e-12, check_interval=5)
+        F, T = gf.gf_functional_theta(h)
+    assert r["converged"] and T[0] < 1e-12 and abs(F[0] - 1) < 1e-10
+
+
+@pytest.mark.parametrize("gauge", GAUGES)
+def test_fix_matches_oracle(gf, synth, orc, gauge):
+    """Config-1 style run (8^4, OR to theta < 1e-12) against the oracle.  MAG
+    converges about twenty times more slowly; it runs on 4^3 x 8."""
+    dims = (4, 4, 4, 8) if gauge == "mag" else (8, 8, 8, 8)
+    omega = 1.35 if gauge == "mag" else 1.7
+    U = synth.links(dims, "smooth", 0.3, 0)
+    orc.random_gauge_transform(U, 100)
+    W = U.copy()
+    n_or, F_or, th_or = orc.fix(W, gauge, "or", omega, 1e-12, max_sweeps=20000, check=10)
+    with Ctx(gf, dims, gauge, "fp64") as h:
+        gf.gf_load_links(h, 0, U)
+        r = gf.gf_fix(h, "or", omega, 1e-12, max_sweeps=20000, check_interval=10)
+        F, T = gf.gf_functional_theta(h)
+        V = store(gf, h, dims)
+    assert r["converged"] and T[0] < 1e-12
+    assert abs(F[0] - F_or) <= 1e-9 * abs(F_or)
+    assert abs(r["sweeps"] - n_or) <= 10
+    # same Gribov copy: the gauge-fixed links agree
+    assert np.abs(V - W).max() < 1e-6
+
+
+@pytest.mark.parametrize("gauge", ["landau", "coulomb"])
+def test_mixed_fix(gf, synth, orc, gauge):
+    dims = (8, 8, 8, 8)
+    U = synth.links(dims, "smooth", 0.3, 0)
+    orc.random_gauge_transform(U, 100)
+    W = U.copy()
+    _, F_or, _ = orc.fix(W, gauge, "or", 1.7, 1e-12, max_sweeps=20000, check=10)
+    with Ctx(gf, dims, gauge, "mixed") as h:
+        gf.gf_load_links(h, 0, U)
+        r = gf.gf_fix(h, "or", 1.7, 1e-12, check_interval=10, reunit_interval=100, switch_theta=1e-8)
+        F, T = gf.gf_functional_theta(h)
+    assert r["converged"] and T[0] < 1e-12 and r["sweeps_fp32"] > 0 and r["sweeps_fp64"] > 0
+    assert abs(F[0] - F_or) <= 1e-9 * abs(F_or)
+
+
+def test_batch_equals_alone(gf, synth, orc):
+    dims = (4, 4, 6, 8)
+    U = synth.links(dims, "smooth", 0.4, 1)
+    with Ctx(gf, dims, "mag", "fp32", n_copies=3) as h:
+        gf.gf_load_links(h, -1, U)
+        gf.gf_random_gauge_transform(h, 77)
+        starts = [store(gf, h, dims, k) for k in range(3)]
+        gf.gf_sweep(h, "sa", 0.8, 3, 5, observables=False)
+        gf.gf_sweep(h, "or", 1.35, 5, observables=False)
+        batched = [store(gf, h, dims, k) for k in range(3)]
+    for k in range(3):
+        with Ctx(gf, dims, "mag", "fp32") as h:
+            gf.gf_set_copy_base(h, k)
+            gf.gf_load_links(h, 0, starts[k])
+            gf.gf_sweep(h, "sa", 0.8, 3, 5, observables=False)
+            gf.gf_sweep(h, "or", 1.35, 5, observables=False)
+            alone = store(gf, h, dims)
+        assert np.array_equal(alone, batched[k])
+
+
+def test_lpt_variants_agree(gf, synth, orc):
+    U = rough(synth, orc, (8, 8, 8, 8))
+    outs = []
+    for lpt in (1, 2, 4, 8):
+        with Ctx(gf, (8, 8, 8, 8), "landau", "fp32") as h:
+            gf.gf_set_links_per_thread(h, lpt)
+            gf.gf_load_links(h, 0, U)
+            gf.gf_sweep(h, "or", 1.7, 5, observables=False)
+            outs.append(store(gf, h, (8, 8, 8, 8)))
+    for o in outs[1:]:
+        assert np.abs(o - outs[0]).max() < 5e-5
+
+
+def test_autotune_restores_links(gf, synth, orc):
+    U = rough(synth, orc, (8, 8, 8, 16))
+    with Ctx(gf, (8, 8, 8, 16), "landau", "fp32") as h:
+        gf.gf_load_links(h, 0, U)
+        best, ms = gf.gf_autotune(h, "or")
+        assert best in (1, 2, 4, 8) and ms > 0
+        V = store(gf, h, (8, 8, 8, 16))
+        assert gf.gf_get_links_per_thread(h) == best
+    assert np.abs(V - U).max() < 3e-7
+
+
+def test_torch_owned_memory(gf, synth, orc):
+    """gf_create_ext with a PyTorch buffer and stream gives the same result."""
+    U = rough(synth, orc, DIMS)
+    W = U.copy()
+    orc.sweep(W, "landau", "or", 1.7, 2)
+    with gf.GaugeField(DIMS, "landau", "fp64") as field:
+        gf.gf_load_links(field.h, 0, U)
+        gf.gf_sweep(field.h, "or", 1.7, 2, observables=False)
+        V = store(gf, field.h, DIMS)
+    assert np.abs(V - W).max() <= 1e-12
+
+
+def test_device_load_store(gf, synth, orc):
+    import torch
+
+    U = rough(synth, orc, DIMS)
+    t = torch.from_numpy(U.view(np.float64).copy()).cuda()
+    out = torch.empty_like(t)
+    with Ctx(gf, DIMS, "landau", "fp64") as h:
+        gf.gf_load_links_device(h, 0, t.data_ptr())
+        gf.gf_store_links_device(h, 0, out.data_ptr())
+    torch.cuda.synchronize()
+    V = out.cpu().numpy().view(np.complex128).reshape(U.shape)
+    assert np.abs(V - U).max() < 1e-14
+
+
+def test_sweep_index_resume(gf, synth, orc):
+    U = rough(synth, orc, DIMS)
+    with Ctx(gf, DIMS, "landau", "fp64") as h:
+        gf.gf_load_links(h, 0, U)
+        gf.gf_sweep(h, "sr", 0.5, 5, 3, observables=False)
+        A = store(gf, h, DIMS)
+    with Ctx(gf, DIMS, "landau", "fp64") as h:
+        gf.gf_load_links(h, 0, U)
+        gf.gf_sweep(h, "sr", 0.5, 2, 3, observables=False)
+        B = store(gf, h, DIMS)
+    with Ctx(gf, DIMS, "landau", "fp64") as h:
+        gf.gf_load_links(h, 0, B)
+        gf.gf_set_sweep_index(h, 2)
+        gf.gf_sweep(h, "sr", 0.5, 3, 3, observables=False)
+        C = store(gf, h, DIMS)
+    assert np.abs(A - C).max() < 1e-13
+
+
+def test_invalid_params(gf):
+    with Ctx(gf, (4, 4, 4, 4), "landau", "fp64") as h:
+        for algo, p in [("or", 2.5), ("or", 0.5), ("sr", 1.5), ("sa", 0.0), ("sa", -1.0)]:
+            with pytest.raises(gf.GFError) as e:
+                gf.gf_sweep(h, algo, p, 1)
+            assert e.value.code == gf.GF_EINVAL
+        with pytest.raises(gf.GFError):
+            gf.gf_store_links(h, 1, np.empty((4, 4, 4, 4, 4, 3, 3), np.complex128))
