@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark of the gauge-fixing hot path on GB300.
+
+Workload (the configuration the headline metric is quoted on): a 32^3 x 64
+SU(3) lattice, links exp(i eps H) with eps = 0.35 (seed 1), gauge fixed to
+Landau gauge by overrelaxation (omega = 1.7) until theta < 1e-12, in mixed
+precision: FP32 sweeps with 12-real links and FP64 re-unitarisation every
+100 sweeps, FP64 theta/functional, and FP64 final sweeps.
+
+One step = one complete gauge fixing of that lattice from a fresh random
+point on its gauge orbit (Haar g(x), a different seed per step):
+  restore the links from the copy resident in HBM -> random gauge transform
+  -> sweeps with theta checks, re-unitarisation and the FP32 -> FP64 switch
+  -> theta < 1e-12.
+value = site-updates/s over the timed steps; the JSON line also carries
+time-to-theta (mixed, and plain FP64 measured once), the roofline of the
+dominant kernel, sampled clocks, an end-to-end number through host buffers
+and the FP64 CPU oracle timed on a bounded sample.
+
+Multi-GPU (torchrun): every rank fixes its own copies (independent
+problems, weak scaling); the only cross-rank traffic is the barrier and the
+max over ranks of the elapsed time.
+
+--impl reference times the FP64 CPU oracle (the plain reference this
+project checks against) on the host cores, on this same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="landau_or_32c3x64_mixed", dims=(64, 32, 32, 32), gauge="landau", eps=0.35,
+                field_seed=1, omega=1.7, theta=1e-12, switch_theta=1e-8, reunit=100, check=20)
+METRIC = "site-updates/s & HBM GB/s (mixed vs FP64); time-to-θ<1e-12; job p50/p99"
+BYTES_PER_SU = {"fp32": 768, "fp64": 1536}  # 8 links x 12 reals x (load + store)
+FLOP_PER_SU = 2274  # App. A: 192 gather + 66 OR + 2016 apply
+FP64_PEAK_TFLOPS = 1.25  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal table)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("gf_device.cuh", "gf_sweep.cuh"):
+        with open(os.path.join(ROOT, "paper_1212_5221_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kind):
+    """Per-launch DRAM bytes of the sweep kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(kind)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch_full_size")
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"gf_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    try:
+                        rows.append((float(p[1]), float(p[2]), p[5:9]))
+                    except ValueError:
+                        pass
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        load = [r[0] for r in rows] or [0]
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(dims, omega, seconds_target=20.0):
+    """Time the FP64 oracle (as it stands, one thread) on whole sweeps of the
+    workload's lattice; run in a fresh process so no GPU state is shared."""
+    code = f"""
+import sys, time, json
+sys.path.insert(0, {ROOT!r})
+import oracle
+from paper_1212_5221_gb300 import inputs
+U = inputs.links({tuple(dims)!r}, "smooth", {WORKLOAD['eps']}, {WORKLOAD['field_seed']})
+oracle.random_gauge_transform(U, 1000)
+oracle.sweep(U, "landau", "or", {omega}, 1)  # warm-up
+n, t0 = 0, time.time()
+while True:
+    oracle.sweep(U, "landau", "or", {omega}, 1, n + 1)
+    n += 1
+    if time.time() - t0 > {seconds_target}:
+        break
+dt = time.time() - t0
+print(json.dumps(dict(sweeps=n, seconds=dt)))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        log("cpu baseline failed:", r.stderr[-500:])
+        return None
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    V = int(np.prod(dims))
+    return {"value": d["sweeps"] * V / d["seconds"], "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{d['sweeps']} FP64 OR sweeps of the {'x'.join(map(str, dims[::-1]))} lattice "
+                      f"(after 1 warm-up sweep), {d['seconds']:.1f} s, single thread"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle on this workload, rank 0 only."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1212_5221_gb300 import inputs
+
+    oracle.build()
+    dims = WORKLOAD["dims"]
+    V = int(np.prod(dims))
+    U = inputs.links(dims, "smooth", WORKLOAD["eps"], WORKLOAD["field_seed"])
+    oracle.random_gauge_transform(U, 1000)
+    # one step = one FP64 OR sweep of the whole lattice (a bounded sample of a fix run)
+    for k in range(args.warmup):
+        oracle.sweep(U, "landau", "or", WORKLOAD["omega"], 1, k)
+    t0 = time.time()
+    for k in range(args.steps):
+        oracle.sweep(U, "landau", "or", WORKLOAD["omega"], 1, args.warmup + k)
+    dt = time.time() - t0
+    value = args.steps * V / dt
+    sample = f"{args.steps} FP64 OR sweeps of the 32^3x64 lattice after {args.warmup} warm-up sweeps"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "lattice": "32^3x64", "gauge": "landau", "omega": 1.7,
+                       "step": "one FP64 overrelaxation sweep (oracle)"},
+            "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1212_5221_gb300 import build, gf, inputs
+
+    build.build_all()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dims = WORKLOAD["dims"]
+    V = int(np.prod(dims))
+    W = WORKLOAD
+
+    U = inputs.links(dims, "smooth", W["eps"], W["field_seed"])
+    src = torch.from_numpy(U.view(np.float64).reshape(-1)).to(dev)  # resident input (natural order, FP64)
+    field = gf.GaugeField(dims, W["gauge"], args.precision, device=dev)
+    h = field.h
+    fix_kw = dict(algo="or", param=W["omega"], theta_target=W["theta"], max_sweeps=args.max_sweeps,
+                  check_interval=W["check"], reunit_interval=W["reunit"], switch_theta=args.switch_theta)
+
+    def step(k):
+        gf.gf_load_links_device(h, 0, src.data_ptr())
+        gf.gf_random_gauge_transform(h, 1000 + k + 100000 * rank)
+        return gf.gf_fix(h, **fix_kw)
+
+    # launch shape: autotune both storage precisions once (setup, untimed)
+    gf.gf_load_links_device(h, 0, src.data_ptr())
+    gf.gf_random_gauge_transform(h, 999)
+    lpt32, _ = gf.gf_autotune(h, "or")
+    log(f"[rank {rank}] autotuned links/thread FP32 = {lpt32}")
+
+    for k in range(args.warmup):
+        r = step(-1 - k)
+        log(f"[rank {rank}] warm-up {k}: {r['sweeps']} sweeps ({r['sweeps_fp32']} FP32), {r['seconds']:.2f} s")
+
+    dist = torch.distributed.is_initialized()
+    if dist:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gf.gf_set_profiling(h, True)
+    n0 = gf.gf_launch_count(h)
+    results = []
+    with Clocks(local_rank) as clocks:
+        start.record(field.stream)
+        t0 = time.time()
+        for k in range(args.steps):
+            results.append(step(k))
+        stop.record(field.stream)
+        torch.cuda.synchronize()
+        wall = time.time() - t0
+    elapsed = start.elapsed_time(stop) / 1e3
+    launches = gf.gf_launch_count(h) - n0
+    stats = {kind: gf.gf_kernel_stats(h, kind) for kind in range(5)}
+    gf.gf_set_profiling(h, False)
+    su = sum(r["site_updates"] for r in results)
+    sweeps32 = sum(r["sweeps_fp32"] for r in results)
+    sweeps64 = sum(r["sweeps_fp64"] for r in results)
+    if dist:
+        t = torch.tensor([elapsed, float(su)], device=dev, dtype=torch.float64)
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        tsum = t.clone()
+        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
+        elapsed_all, su_all = float(tmax[0]), float(tsum[1])
+    else:
+        elapsed_all, su_all = elapsed, float(su)
+
+    # roofline of the dominant kernel (largest total device time)
+    peaks, peak_src = measured_peaks()
+    kind_names = {0: "sweep_fp32", 1: "sweep_fp64", 2: "observables", 3: "reunitarize", 4: "promote"}
+    dom = max(stats, key=lambda k: stats[k][1])
+    n_l, ms_l = stats[dom]
+    avg_s = ms_l / max(n_l, 1) / 1e3
+    sites_per_launch = V // 2  # one sublattice
+    if dom == 0:
+        roof = {"bound": "hbm", "achieved": BYTES_PER_SU["fp32"] * sites_per_launch / avg_s / 1e9,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+        roof["traffic"] = ncu_traffic("sweep_fp32")
+    elif dom == 1:
+        roof = {"bound": "alu", "achieved": FLOP_PER_SU * sites_per_launch / avg_s / 1e12,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
+        roof["traffic"] = ncu_traffic("sweep_fp64")
+    else:
+        roof = {"bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None}
+    if roof["achieved"] is not None:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = kind_names[dom]
+    roof["avg_launch_ms"] = avg_s * 1e3
+    roof["peak_source"] = (f"{peak_src} MEASURED_PEAKS.json hbm_gbs" if dom != 1 else
+                           "FP64 ALU: nominal 1.25 TFLOP/s (2 FMA/clk/SM x 152 SMs x 2.07 GHz)")
+    kernel_ms = {kind_names[k]: {"launches": stats[k][0], "ms": round(stats[k][1], 3)} for k in stats}
+    sweep32_gbs = None
+    if stats[0][0]:
+        sweep32_gbs = BYTES_PER_SU["fp32"] * sites_per_launch / (stats[0][1] / stats[0][0] / 1e3) / 1e9
+    sweep64_gbs = None
+    if stats[1][0]:
+        sweep64_gbs = BYTES_PER_SU["fp64"] * sites_per_launch / (stats[1][1] / stats[1][0] / 1e3) / 1e9
+
+    out = {}
+    if rank == 0:
+        # plain FP64 time-to-theta on the same problem (one run, untimed by the steps)
+        fp64 = None
+        if args.fp64_baseline:
+            f64 = gf.GaugeField(dims, W["gauge"], "fp64", device=dev)
+            gf.gf_load_links_device(f64.h, 0, src.data_ptr())
+            gf.gf_random_gauge_transform(f64.h, 1000)
+            kw = dict(fix_kw)
+            r64 = gf.gf_fix(f64.h, **kw)
+            fp64 = {"seconds": r64["seconds"], "sweeps": r64["sweeps"],
+                    "site_updates_per_s": r64["site_updates"] / r64["seconds"]}
+            f64.close()
+        # end to end through the C ABI with pinned host buffers
+        e2e = None
+        if args.e2e_steps > 0:
+            host_in = torch.from_numpy(U.view(np.float64).reshape(-1)).pin_memory()
+            host_out = torch.empty_like(host_in).pin_memory()
+            hin = host_in.numpy().view(np.complex128).reshape(U.shape)
+            hout = host_out.numpy().view(np.complex128).reshape(U.shape)
+            torch.cuda.synchronize()
+            t0 = time.time()
+            su_e = 0
+            for k in range(args.e2e_steps):
+                gf.gf_load_links(h, 0, hin)
+                gf.gf_random_gauge_transform(h, 1000 + k)
+                r = gf.gf_fix(h, **fix_kw)
+                gf.gf_store_links(h, 0, hout)
+                su_e += r["site_updates"]
+            te = time.time() - t0
+            e2e = {"value": su_e / te, "unit": "site-updates/s", "h2d_bytes_per_step": int(U.nbytes),
+                   "d2h_bytes_per_step": int(U.nbytes), "steps": args.e2e_steps,
+                   "seconds_per_step": te / args.e2e_steps}
+        cpu = cpu_baseline(dims, W["omega"], args.cpu_seconds) if args.cpu_seconds > 0 else None
+        mixed_tt = elapsed / args.steps
+        out = {
+            "metric": METRIC,
+            "value": su_all / elapsed_all,
+            "unit": "site-updates/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": elapsed_all / args.steps * 1e3,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else ("f64" if args.precision == "fp64" else "f32"),
+            "data": "synthetic",
+            "config": {"workload": W["name"], "lattice": "32^3x64", "gauge": "landau", "algorithm": "OR",
+                       "omega": W["omega"], "theta_target": W["theta"], "precision": args.precision,
+                       "switch_theta": args.switch_theta, "reunit_interval": W["reunit"],
+                       "check_interval": W["check"], "field": f"exp(i 0.35 H), seed {W['field_seed']}, "
+                       "then Haar g(x) per step", "l2": "inputs larger than L2 (403 MB FP32 links)",
+                       "parallelism": f"replicas x{world}"},
+            "time_to_theta_s": {"mixed": mixed_tt, "fp64": fp64["seconds"] if fp64 else None,
+                                "speedup_mixed_vs_fp64": (fp64["seconds"] / mixed_tt) if fp64 else None},
+            "sweeps_per_step": {"fp32": sweeps32 / args.steps, "fp64": sweeps64 / args.steps},
+            "hbm_gbs": {"sweep_fp32": sweep32_gbs, "sweep_fp64": sweep64_gbs},
+            "fp64_run": fp64,
+            "roofline": roof,
+            "kernel_ms": kernel_ms,
+            "gpu_launches": int(launches),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks.summary(),
+            "wall_s": wall,
+        }
+        print(json.dumps(out), flush=True)
+    field.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64", "fp32"], default="mixed")
+    ap.add_argument("--switch-theta", type=float, default=WORKLOAD["switch_theta"])
+    ap.add_argument("--max-sweeps", type=int, default=40000)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-fp64-baseline", dest="fp64_baseline", action="store_false")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

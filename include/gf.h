@@ -206,6 +206,24 @@ int gf_fix(gf_ctx* ctx, const gf_fix_params* params, gf_fix_result* result);
  * the call allocates and frees its own device buffers. */
 int gf_philox(uint64_t seed, const uint32_t* counters, size_t n, uint32_t* out);
 
+/* Per-kernel timing.  With profiling on, every launch of the classes below
+ * is bracketed by CUDA events on the context's stream; gf_kernel_stats
+ * returns the number of launches and their summed device time since
+ * profiling was (re)enabled.  gf_set_profiling resets the totals. */
+enum {
+  GF_KERNEL_SWEEP_FP32 = 0,   /* one half-sweep (one sublattice), FP32 storage */
+  GF_KERNEL_SWEEP_FP64 = 1,   /* one half-sweep, FP64 storage */
+  GF_KERNEL_OBSERVABLES = 2,  /* exact F/theta pass (both kernels) */
+  GF_KERNEL_REUNITARIZE = 3,
+  GF_KERNEL_OTHER = 4,        /* FP32 -> FP64 promotion */
+  GF_KERNEL_KINDS = 5
+};
+int gf_set_profiling(gf_ctx* ctx, int on);
+int gf_kernel_stats(gf_ctx* ctx, int kind, uint64_t* launches, double* total_ms);
+
+/* Number of kernels this context has launched since it was created. */
+int gf_launch_count(gf_ctx* ctx, uint64_t* n);
+
 /* Geometry and state queries. */
 int gf_get_info(gf_ctx* ctx, int dims[4], int* n_copies, int* gauge, int* precision, int* storage_fp64);
 

@@ -120,6 +120,17 @@ struct gf_ctx {
   uint64_t sweep_index = 0;
   uint32_t copy_base = 0;  // Philox copy id of copy 0
   int lpt[2][5] = {{0}};  // [fp64][algo] chosen links per thread, 0 = default
+  // optional per-kernel timing: CUDA events around every launch of a class
+  uint64_t launch_count = 0;  // every kernel this context launched
+  bool profiling = false;
+  struct Pending {
+    cudaEvent_t a, b;
+    int kind;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  uint64_t prof_launches[GF_KERNEL_KINDS] = {0};
+  double prof_ms[GF_KERNEL_KINDS] = {0};
 
   void* links() const { return fp64 ? links64 : links32; }
   size_t copy_block_bytes() const {
@@ -129,10 +140,51 @@ struct gf_ctx {
 
 namespace {
 
+cudaEvent_t take_event(gf_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Start / end a timed launch of the given kind (no-ops unless profiling).
+cudaEvent_t prof_begin(gf_ctx* c) {
+  if (!c->profiling) return nullptr;
+  cudaEvent_t e = take_event(c);
+  cudaEventRecord(e, c->st);
+  return e;
+}
+
+void prof_end(gf_ctx* c, cudaEvent_t start, int kind) {
+  if (!c->profiling || !start) return;
+  cudaEvent_t e = take_event(c);
+  cudaEventRecord(e, c->st);
+  c->pending.push_back({start, e, kind});
+}
+
+// Fold completed event pairs into the per-kind totals (call after a sync).
+void prof_collect(gf_ctx* c) {
+  for (auto& p : c->pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->prof_ms[p.kind] += ms;
+      c->prof_launches[p.kind]++;
+    }
+    c->event_pool.push_back(p.a);
+    c->event_pool.push_back(p.b);
+  }
+  c->pending.clear();
+  cudaGetLastError();
+}
+
 int default_lpt(const gf_ctx* c, int algo) {
   int v = c->lpt[c->fp64][algo];
   if (v) return v;
-  return c->fp64 ? 2 : 1;
+  return c->fp64 ? 8 : 4;  // fastest on GB300 for the 32^3 x 64 Landau sweep
 }
 
 int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, uint32_t sweep, int lpt) {
@@ -150,7 +202,10 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     a.k0 = (uint32_t)seed;
     a.k1 = (uint32_t)(seed >> 32);
     a.sweep = sweep;
+    cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<double>(a, c->gauge, kalgo, lpt, c->st);
+    prof_end(c, t0, GF_KERNEL_SWEEP_FP64);
+    c->launch_count++;
   } else {
     gfk::SweepArgs<float> a;
     a.links = static_cast<float4*>(c->links32);
@@ -164,7 +219,10 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     a.k0 = (uint32_t)seed;
     a.k1 = (uint32_t)(seed >> 32);
     a.sweep = sweep;
+    cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<float>(a, c->gauge, kalgo, lpt, c->st);
+    prof_end(c, t0, GF_KERNEL_SWEEP_FP32);
+    c->launch_count++;
   }
   if (e != cudaSuccess) return fail(GF_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
   return GF_OK;
@@ -183,15 +241,19 @@ int full_sweep(gf_ctx* c, int kalgo, int api_algo, double param, uint64_t seed, 
 }
 
 int observables(gf_ctx* c, std::vector<double>& per_ct) {
+  cudaEvent_t t0 = prof_begin(c);
   cudaError_t e = c->fp64 ? gfk::launch_observables<double>(c->links64, c->G, c->NS, c->gauge, c->ncopies,
                                                              c->partial, c->obs_d, c->st)
                           : gfk::launch_observables<float>(c->links32, c->G, c->NS, c->gauge, c->ncopies,
                                                             c->partial, c->obs_d, c->st);
   if (e != cudaSuccess) return fail(GF_ECUDA, "observables launch: %s", cudaGetErrorString(e));
+  prof_end(c, t0, GF_KERNEL_OBSERVABLES);
+  c->launch_count += 2;
   per_ct.resize((size_t)c->ncopies * c->dims[0] * 2);
   GF_CUDA(cudaMemcpyAsync(per_ct.data(), c->obs_d, per_ct.size() * sizeof(double), cudaMemcpyDeviceToHost,
                           c->st));
   GF_CUDA(cudaStreamSynchronize(c->st));
+  prof_collect(c);
   return GF_OK;
 }
 
@@ -221,6 +283,7 @@ int coulomb_fold(gf_ctx* c) {
   cudaError_t e = c->fp64 ? gfk::launch_coulomb_fold<double>(c->links64, c->G, c->ncopies, c->st)
                           : gfk::launch_coulomb_fold<float>(c->links32, c->G, c->ncopies, c->st);
   if (e != cudaSuccess) return fail(GF_ECUDA, "coulomb fold: %s", cudaGetErrorString(e));
+  c->launch_count += 2;
   return GF_OK;
 }
 
@@ -229,6 +292,7 @@ int set_identity_slots(gf_ctx* c, int first, int last) {
     cudaError_t e = c->fp64 ? gfk::launch_identity_slot<double>(c->links64, c->G, c->NS, s, c->ncopies, c->st)
                             : gfk::launch_identity_slot<float>(c->links32, c->G, c->NS, s, c->ncopies, c->st);
     if (e != cudaSuccess) return fail(GF_ECUDA, "identity: %s", cudaGetErrorString(e));
+    c->launch_count++;
   }
   return GF_OK;
 }
@@ -320,6 +384,7 @@ int import_slab(gf_ctx* c, int copy, int t0, int nt, const double* dev) {
   cudaError_t e = c->fp64 ? gfk::launch_import<double>(dev, c->links64, c->G, c->NS, copy, t0, nt, c->st)
                           : gfk::launch_import<float>(dev, c->links32, c->G, c->NS, copy, t0, nt, c->st);
   if (e != cudaSuccess) return fail(GF_ECUDA, "import: %s", cudaGetErrorString(e));
+  c->launch_count++;
   return GF_OK;
 }
 
@@ -327,6 +392,7 @@ int export_slab(gf_ctx* c, int copy, int t0, int nt, double* dev) {
   cudaError_t e = c->fp64 ? gfk::launch_export<double>(dev, c->links64, c->G, c->NS, copy, t0, nt, c->st)
                           : gfk::launch_export<float>(dev, c->links32, c->G, c->NS, copy, t0, nt, c->st);
   if (e != cudaSuccess) return fail(GF_ECUDA, "export: %s", cudaGetErrorString(e));
+  c->launch_count++;
   return GF_OK;
 }
 
@@ -381,9 +447,12 @@ int api_sweep(gf_ctx* c, int algo, double param, uint64_t seed) {
 
 int reunitarize(gf_ctx* c) {
   const uint64_t nmat = (uint64_t)c->ncopies * 2 * c->NS * c->G.Vh;
+  cudaEvent_t t0 = prof_begin(c);
   cudaError_t e = c->fp64 ? gfk::launch_reunitarize<double>(c->links64, c->G.Vh, nmat, c->st)
                           : gfk::launch_reunitarize<float>(c->links32, c->G.Vh, nmat, c->st);
   if (e != cudaSuccess) return fail(GF_ECUDA, "reunitarize: %s", cudaGetErrorString(e));
+  prof_end(c, t0, GF_KERNEL_REUNITARIZE);
+  c->launch_count++;
   return GF_OK;
 }
 
@@ -391,8 +460,11 @@ int promote(gf_ctx* c) {
   if (c->fp64) return GF_OK;
   if (c->prec != GF_MIXED) return fail(GF_EINVAL, "gf_promote needs a GF_MIXED context");
   const uint64_t nmat = (uint64_t)c->ncopies * 2 * c->NS * c->G.Vh;
+  cudaEvent_t t0 = prof_begin(c);
   cudaError_t e = gfk::launch_promote(c->links32, c->links64, c->G.Vh, nmat, c->st);
   if (e != cudaSuccess) return fail(GF_ECUDA, "promote: %s", cudaGetErrorString(e));
+  prof_end(c, t0, GF_KERNEL_OTHER);
+  c->launch_count++;
   c->fp64 = true;
   return GF_OK;
 }
@@ -427,6 +499,8 @@ int gf_create_ext(const int dims[4], int n_copies, gf_gauge gauge, gf_precision 
 void gf_destroy(gf_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
+  prof_collect(c);
+  for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   if (c->owned) cudaFree(c->owned);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
   delete c;
@@ -505,6 +579,7 @@ int gf_random_gauge_transform(gf_ctx* c, uint64_t seed) {
   cudaError_t e = c->fp64 ? gfk::launch_haar_transform<double>(c->links64, c->G, c->NS, c->ncopies, c->copy_base, seed, c->st)
                           : gfk::launch_haar_transform<float>(c->links32, c->G, c->NS, c->ncopies, c->copy_base, seed, c->st);
   if (e != cudaSuccess) return fail(GF_ECUDA, "random gauge transform: %s", cudaGetErrorString(e));
+  c->launch_count += 2;
   GF_CUDA(cudaStreamSynchronize(c->st));
   return GF_OK;
 }
@@ -779,6 +854,38 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
   R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   if (res) *res = R;
   if (!R.converged) return fail(GF_ENOTCONV, "theta_target not reached in %d sweeps", R.sweeps);
+  return GF_OK;
+}
+
+int gf_set_profiling(gf_ctx* c, int on) {
+  int r = check_ctx(c);
+  if (r) return r;
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  prof_collect(c);
+  c->profiling = on != 0;
+  for (int k = 0; k < GF_KERNEL_KINDS; ++k) {
+    c->prof_launches[k] = 0;
+    c->prof_ms[k] = 0;
+  }
+  return GF_OK;
+}
+
+int gf_launch_count(gf_ctx* c, uint64_t* n) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!n) return fail(GF_EINVAL, "n is NULL");
+  *n = c->launch_count;
+  return GF_OK;
+}
+
+int gf_kernel_stats(gf_ctx* c, int kind, uint64_t* launches, double* total_ms) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (kind < 0 || kind >= GF_KERNEL_KINDS) return fail(GF_EINVAL, "bad kernel kind %d", kind);
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  prof_collect(c);
+  if (launches) *launches = c->prof_launches[kind];
+  if (total_ms) *total_ms = c->prof_ms[kind];
   return GF_OK;
 }
 

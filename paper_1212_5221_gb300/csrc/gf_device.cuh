@@ -282,6 +282,17 @@ __device__ __forceinline__ quat<R> mag_max(R x1, R x2, R x3, R& r) {
   return {top * inv, v1 * inv, v2 * inv, R(0)};
 }
 
+// MAG microcanonical step: the square of the maximiser above.  With h the
+// rotation by the angle a between x and +z about an axis in the xy-plane,
+// h^2 is the rotation by 2a, whose quaternion is (x3, -x2, x1, 0)/|x|; this
+// form needs no half angles and loses no accuracy when x3 < 0.
+template <typename R>
+__device__ __forceinline__ quat<R> mag_micro(R x1, R x2, R x3, R r) {
+  if (r == R(0)) return qidentity<R>();
+  R inv = R(1) / r;
+  return {x3 * inv, -x2 * inv, x1 * inv, R(0)};
+}
+
 // Kennedy-Pendleton heat bath for x0 ~ sqrt(1-x0^2) exp(alpha x0), at most
 // KP_TRIALS trials (x0 = 1 if none is accepted).
 template <typename R>

@@ -150,11 +150,11 @@ __global__ void __launch_bounds__(BLOCK) sweep_kernel(const SweepArgs<R> a) {
       R r;
       quat<R> m = mag_max(x1, x2, x3, r);
       if (ALGO == ALG_OR) g = rule_or(m, a.param);
-      else if (ALGO == ALG_MICRO) g = rule_micro(m);
+      else if (ALGO == ALG_MICRO) g = mag_micro(x1, x2, x3, r);
       else if (ALGO == ALG_SR) {
         double ua, ub;
         rng.draw2(TAG_SR, (uint32_t)sub, 0, ua, ub);
-        g = ((R)ua < a.param) ? rule_micro(m) : rule_or(m, R(1));
+        g = ((R)ua < a.param) ? mag_micro(x1, x2, x3, r) : rule_or(m, R(1));
       } else {
         g = rule_sa_mag(m, r, a.param, rng, (uint32_t)sub);
       }

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libgf.so")
 GF_LANDAU, GF_COULOMB, GF_MAG = 0, 1, 2
 GF_FP64, GF_FP32, GF_MIXED = 0, 1, 2
 GF_RELAX, GF_OR, GF_MICRO, GF_SR, GF_SA = 0, 1, 2, 3, 4
+GF_KERNEL_SWEEP_FP32, GF_KERNEL_SWEEP_FP64, GF_KERNEL_OBSERVABLES, GF_KERNEL_REUNITARIZE, GF_KERNEL_OTHER = range(5)
 GF_OK, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_ETIMEOUT, GF_ENOTCONV, GF_ENOSYS = range(7)
 
 GAUGES = {"landau": GF_LANDAU, "coulomb": GF_COULOMB, "mag": GF_MAG}
@@ -84,6 +85,9 @@ _SIG = {
     "gf_fix": [_P, ctypes.POINTER(gf_fix_params), ctypes.POINTER(gf_fix_result)],
     "gf_get_info": [_P, _PI, _PI, _PI, _PI, _PI],
     "gf_philox": [ctypes.c_uint64, _P, ctypes.c_size_t, _P],
+    "gf_set_profiling": [_P, _I],
+    "gf_kernel_stats": [_P, _I, ctypes.POINTER(ctypes.c_uint64), _PD],
+    "gf_launch_count": [_P, ctypes.POINTER(ctypes.c_uint64)],
 }
 _lib = None
 
@@ -303,6 +307,24 @@ def gf_get_info(h):
     _check(lib().gf_get_info(h, dims, ctypes.byref(n), ctypes.byref(g), ctypes.byref(p), ctypes.byref(f)),
            "gf_get_info")
     return dict(dims=tuple(dims), n_copies=n.value, gauge=g.value, precision=p.value, storage_fp64=bool(f.value))
+
+
+def gf_set_profiling(h, on=True):
+    _check(lib().gf_set_profiling(h, 1 if on else 0), "gf_set_profiling")
+
+
+def gf_kernel_stats(h, kind):
+    """(launches, total device ms) of one kernel class since profiling was enabled."""
+    n = ctypes.c_uint64()
+    ms = ctypes.c_double()
+    _check(lib().gf_kernel_stats(h, int(kind), ctypes.byref(n), ctypes.byref(ms)), "gf_kernel_stats")
+    return n.value, ms.value
+
+
+def gf_launch_count(h):
+    n = ctypes.c_uint64()
+    _check(lib().gf_launch_count(h, ctypes.byref(n)), "gf_launch_count")
+    return n.value
 
 
 def gf_philox(seed, counters):
