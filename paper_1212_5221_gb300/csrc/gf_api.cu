@@ -821,13 +821,15 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
     }
     if (R.sweeps >= P->max_sweeps) break;
     if (!c->fp64 && c->prec == GF_MIXED) {
-      if (worst < best_fp32 * 0.9) {
+      // switch below switch_theta, or once FP32 has stopped improving theta
+      // (its rounding floor) for 25 consecutive checks
+      if (worst < best_fp32) {
         best_fp32 = worst;
         stall = 0;
       } else {
         stall++;
       }
-      if (worst < P->switch_theta || stall >= 5 || !std::isfinite(worst)) {
+      if (worst < P->switch_theta || stall >= 25 || !std::isfinite(worst)) {
         if ((r = promote(c))) return r;
         continue;  // re-evaluate theta in FP64
       }
