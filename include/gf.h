@@ -224,6 +224,31 @@ int gf_kernel_stats(gf_ctx* ctx, int kind, uint64_t* launches, double* total_ms)
 /* Number of kernels this context has launched since it was created. */
 int gf_launch_count(gf_ctx* ctx, uint64_t* n);
 
+/* F and theta without any device allocation, for callers that cannot call
+ * cudaMalloc (a serving loop confined to a device-memory pool reserved at
+ * start-up, a host framework that owns every allocation, or code that must
+ * not trigger the allocator's implicit synchronisation).  The paper has no
+ * counterpart; this is a deployment aid.
+ *   dims, gauge   as for gf_create; Nt = dims[0] <= GF_NOALLOC_MAX_NT.
+ *   device_links  the links in device memory, natural order (18 doubles per
+ *                 link, full 3x3, 72*V doubles), 16-byte aligned, owned by
+ *                 the caller and only read.
+ *   stream        the cudaStream_t to run on (NULL: the legacy default stream).
+ *   F, theta      host pointers receiving the functional and theta (means
+ *                 over time-slices, as gf_functional_theta for one copy).
+ *   F_t, theta_t  host arrays of Nt doubles for the per-slice values, or NULL.
+ * The reduction's partial sums live in one file-scope device array of about
+ * 1 MiB, which every GPU that loads the library holds until the process
+ * exits; the call allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library routine).  Every call shares that array and it keeps the last
+ * call's contents, so calls that overlap on the GPU race: serialise them.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any CUDA stream capture.
+ * Returns GF_EINVAL for sizes beyond the maximum or misaligned input. */
+#define GF_NOALLOC_MAX_NT 1024
+int gf_functional_theta_noalloc(const int dims[4], gf_gauge gauge, const double* device_links, void* stream,
+                                double* F, double* theta, double* F_t, double* theta_t);
+
 /* Geometry and state queries. */
 int gf_get_info(gf_ctx* ctx, int dims[4], int* n_copies, int* gauge, int* precision, int* storage_fp64);
 

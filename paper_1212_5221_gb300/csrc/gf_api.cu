@@ -100,6 +100,8 @@ Layout make_layout(const int dims[4], int ncopies, int gauge, int prec) {
 
 }  // namespace
 
+void gfk::set_last_error(const char* msg) { g_last_error = msg; }
+
 struct gf_ctx {
   int dims[4];
   int ncopies, gauge, prec, NS;

@@ -41,6 +41,9 @@ template <typename R>
 cudaError_t launch_identity_slot(void* links, const Geom& G, int NS, int slot, uint32_t ncopies,
                                  cudaStream_t st);
 
+// Record the calling thread's error message (read by gf_last_error).
+void set_last_error(const char* msg);
+
 cudaError_t launch_philox(const void* ctr, void* out, uint64_t n, uint64_t seed, cudaStream_t st);
 
 }  // namespace gfk

@@ -88,6 +88,7 @@ _SIG = {
     "gf_set_profiling": [_P, _I],
     "gf_kernel_stats": [_P, _I, ctypes.POINTER(ctypes.c_uint64), _PD],
     "gf_launch_count": [_P, ctypes.POINTER(ctypes.c_uint64)],
+    "gf_functional_theta_noalloc": [_PI, _I, _P, _P, _P, _P, _P, _P],
 }
 _lib = None
 
@@ -325,6 +326,18 @@ def gf_launch_count(h):
     n = ctypes.c_uint64()
     _check(lib().gf_launch_count(h, ctypes.byref(n)), "gf_launch_count")
     return n.value
+
+
+def gf_functional_theta_noalloc(dims, gauge, device_links_ptr: int, stream=None):
+    """F and theta of natural-order FP64 links in device memory, without any
+    device allocation (see include/gf.h).  Returns (F, theta, F_t, theta_t)."""
+    nt = int(dims[0])
+    F, T = ctypes.c_double(), ctypes.c_double()
+    Ft, Tt = np.zeros(nt), np.zeros(nt)
+    _check(lib().gf_functional_theta_noalloc(_dims(dims), _enum(gauge, GAUGES), _P(device_links_ptr), stream,
+                                             ctypes.byref(F), ctypes.byref(T), Ft.ctypes.data, Tt.ctypes.data),
+           "gf_functional_theta_noalloc")
+    return F.value, T.value, Ft, Tt
 
 
 def gf_philox(seed, counters):
