@@ -368,6 +368,23 @@ def run_ours(args, rank, world, local_rank):
     field.close()
 
 
+def run_kernel_target(args):
+    """A short, fixed sequence of sweep launches on the workload's lattice,
+    for ncu captures: 3 sweeps of the chosen storage precision."""
+    from paper_1212_5221_gb300 import build, gf, inputs
+
+    build.build_all()
+    dims = WORKLOAD["dims"]
+    U = inputs.links(dims, "smooth", WORKLOAD["eps"], WORKLOAD["field_seed"])
+    h = gf.gf_create(dims, WORKLOAD["gauge"], args.kernel_target)
+    gf.gf_load_links(h, 0, U)
+    gf.gf_random_gauge_transform(h, 1000)
+    gf.gf_sweep(h, "or", WORKLOAD["omega"], 3, observables=False)
+    F, T = gf.gf_functional_theta(h)
+    gf.gf_destroy(h)
+    print(json.dumps({"kernel_target": args.kernel_target, "F": float(F[0]), "theta": float(T[0])}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -380,7 +397,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-fp64-baseline", dest="fp64_baseline", action="store_false")
+    ap.add_argument("--kernel-target", choices=["fp32", "fp64"], default=None,
+                    help="only run 3 sweeps of the workload in this storage precision (for ncu)")
     args = ap.parse_args()
+    if args.kernel_target:
+        run_kernel_target(args)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -168,6 +168,12 @@ int gf_set_copy_base(gf_ctx* ctx, uint32_t base);
  * default.  gf_autotune times the four on a scratch copy of the links and
  * keeps the fastest for each (precision, algorithm) it is asked about. */
 int gf_set_links_per_thread(gf_ctx* ctx, int lpt);
+
+/* The sweep kernels run a persistent grid over tiles of sites and, when on
+ * (the default), prefetch each block's next tile of links into L2 with
+ * bulk prefetches while the current tile is processed.  Results do not
+ * depend on this switch. */
+int gf_set_prefetch(gf_ctx* ctx, int on);
 int gf_get_links_per_thread(gf_ctx* ctx, int* lpt);
 int gf_autotune(gf_ctx* ctx, gf_algo algo, int* best_lpt, double* ms_per_sweep_best);
 

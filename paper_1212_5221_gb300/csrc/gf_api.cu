@@ -121,6 +121,7 @@ struct gf_ctx {
   std::vector<int> active_h;
   uint64_t sweep_index = 0;
   uint32_t copy_base = 0;  // Philox copy id of copy 0
+  int prefetch = 1;        // L2 prefetch of the next tile in the sweep kernels
   int lpt[2][5] = {{0}};  // [fp64][algo] chosen links per thread, 0 = default
   // optional per-kernel timing: CUDA events around every launch of a class
   uint64_t launch_count = 0;  // every kernel this context launched
@@ -204,6 +205,7 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     a.k0 = (uint32_t)seed;
     a.k1 = (uint32_t)(seed >> 32);
     a.sweep = sweep;
+    a.prefetch = c->prefetch;
     cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<double>(a, c->gauge, kalgo, lpt, c->st);
     prof_end(c, t0, GF_KERNEL_SWEEP_FP64);
@@ -221,6 +223,7 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     a.k0 = (uint32_t)seed;
     a.k1 = (uint32_t)(seed >> 32);
     a.sweep = sweep;
+    a.prefetch = c->prefetch;
     cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<float>(a, c->gauge, kalgo, lpt, c->st);
     prof_end(c, t0, GF_KERNEL_SWEEP_FP32);
@@ -696,6 +699,13 @@ int gf_set_copy_base(gf_ctx* c, uint32_t base) {
   int r = check_ctx(c);
   if (r) return r;
   c->copy_base = base;
+  return GF_OK;
+}
+
+int gf_set_prefetch(gf_ctx* c, int on) {
+  int r = check_ctx(c);
+  if (r) return r;
+  c->prefetch = on ? 1 : 0;
   return GF_OK;
 }
 

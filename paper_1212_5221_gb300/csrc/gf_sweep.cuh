@@ -20,6 +20,7 @@ struct SweepArgs {
   R param;            // omega (OR), p (SR), T (SA)
   uint32_t k0, k1;    // Philox key (the seed)
   uint32_t sweep;     // sweep index for the random draws
+  int prefetch;       // 1: prefetch the next tile into L2
 };
 
 // Element offset of (copy, parity, slot, chunk 0, site index).
@@ -63,29 +64,64 @@ __device__ __forceinline__ void left_subgroup_mult(mat3<R>& u, int i, int j, con
 }
 
 // ---------------------------------------------------------------------------
+// L2 prefetch of the links a tile of sites will touch: for every slot and
+// chunk, one cp.async.bulk.prefetch.L2 of the contiguous range of parity
+// indices it covers.  Up-links of sites [sp0, sp0+n) occupy the same range
+// of their arrays; the down-link neighbours x - mu of those sites occupy
+// [sp0 - d_mu - 1, sp0 + n - d_mu + 1) of the other parity's arrays
+// (d_mu = stride_mu / 2 for mu < 3, 0 for z), except for sites on the
+// periodic boundary, which are simply not prefetched.  Ranges are clipped to
+// [0, Vh), so no prefetch leaves the allocation.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+template <typename R, int GAUGE>
+__device__ __forceinline__ void prefetch_tile(const SweepArgs<R>& a, uint32_t copy, uint32_t sp0, uint32_t n,
+                                              int job) {
+  constexpr int NC = store_traits<R>::NC;
+  const int chunk = job % NC;
+  const int k = job / NC;  // slot 0..7: mu = k >> 1, down = k & 1
+  const int mu = k >> 1;
+  const bool down = k & 1;
+  if (GAUGE == COULOMB && mu == 0 && down) return;  // idle slot
+  const int slot = (GAUGE == COULOMB && mu == 0) ? 4 : mu;
+  const int64_t Vh = a.geom.Vh;
+  int64_t lo = sp0, hi = (int64_t)sp0 + n;
+  int par = a.parity;
+  if (down) {
+    const int64_t d = mu == 3 ? 0 : (int64_t)(a.geom.stride[mu] / 2);
+    lo = lo - d - 1;
+    hi = hi - d + 1;
+    par ^= 1;
+  }
+  if (lo < 0) lo = 0;
+  if (hi > Vh) hi = Vh;
+  if (hi <= lo) return;
+  const auto* base = a.links + link_off(copy, par, slot, a.NS, NC, (uint32_t)Vh, 0) + (size_t)chunk * Vh;
+  prefetch_l2(base + lo, (uint32_t)((hi - lo) * 16));
+}
+
+// ---------------------------------------------------------------------------
 // One half-sweep (Alg. 1 for one sublattice).  L = 8/LPT lanes share a site;
-// lane l holds slots l*LPT .. l*LPT+LPT-1 of the site's eight links:
-// slot k < 4 is U_k(x), slot k >= 4 is U_{k-4}(x - k)^dagger, so that every
+// lane l holds slots l*LPT .. l*LPT+LPT-1 of the site's eight links, slot
+// k = 2 mu + d: d = 0 is U_mu(x), d = 1 is U_mu(x - mu)^dagger, so that every
 // slot's K contribution (Eq. Kx) is its (i,j) block and every update is a
 // left multiplication by g.  Per subgroup, the lanes' partial quaternions
 // (Landau/Coulomb) or Pauli vectors (MAG) are summed with an xor butterfly of
 // warp shuffles, which gives bit-identical sums in all lanes, so all lanes
 // compute the same g (Step 1) and apply it to their own slots (Step 2).
 // Coulomb: slot 0 holds the accumulated g(x) of the time-slice sweep (updated,
-// not gathered) and slot 4 is idle; the temporal links are not touched.
+// not gathered) and slot 1 is idle; the temporal links are not touched.
+// The grid is persistent over tiles of BLOCK/L sites; each block prefetches
+// its next tile into L2 while it works on the current one.
 template <typename R, int GAUGE, int ALGO, int LPT>
-__global__ void __launch_bounds__(BLOCK) sweep_kernel(const SweepArgs<R> a) {
-  using Vec = typename store_traits<R>::vec;
+__device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy, uint32_t sp, bool valid,
+                                           int lane) {
   constexpr int NC = store_traits<R>::NC;
   constexpr int L = 8 / LPT;
   const Geom& G = a.geom;
   const uint32_t Vh = G.Vh;
-  const uint64_t tid = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
-  const uint64_t gsite = tid / L;
-  const int lane = (int)(threadIdx.x % L);
-  const uint32_t copy = (uint32_t)(gsite / Vh);
-  const uint32_t sp = (uint32_t)(gsite - (uint64_t)copy * Vh);
-  bool valid = copy < a.ncopies;
   int c[4] = {0, 0, 0, 0};
   uint32_t s = 0;
   if (valid) {
@@ -95,27 +131,30 @@ __global__ void __launch_bounds__(BLOCK) sweep_kernel(const SweepArgs<R> a) {
 
   mat3<R> u[LPT];
   size_t off[LPT];
-  bool use[LPT], gather[LPT], down[LPT];
+  bool use[LPT], gather[LPT];
 #pragma unroll
   for (int j = 0; j < LPT; ++j) {
     const int k = lane * LPT + j;
-    const int mu = k & 3;
-    down[j] = k >= 4;
+    const int mu = k >> 1;
+    const bool down = (LPT >= 2) ? (j & 1) : (k & 1);
     gather[j] = !(GAUGE == COULOMB && mu == 0);
-    use[j] = valid && !(GAUGE == COULOMB && k == 4);
-    int slot = mu;
+    use[j] = valid && !(GAUGE == COULOMB && mu == 0 && down);
+    const int slot = (GAUGE == COULOMB && mu == 0) ? 4 : mu;
     uint32_t ssp = sp;
     int par = a.parity;
-    if (GAUGE == COULOMB && k == 0) slot = 4;  // the accumulated g(x)
-    if (down[j]) {
-      ssp = site_minus(G, s, c, mu) >> 1;
+    if (down) {
+      // x - mu without dynamic indexing of the coordinate arrays
+      const int cm = mu == 0 ? c[0] : mu == 1 ? c[1] : mu == 2 ? c[2] : c[3];
+      const int nm = mu == 0 ? G.n[0] : mu == 1 ? G.n[1] : mu == 2 ? G.n[2] : G.n[3];
+      const uint32_t st = mu == 0 ? G.stride[0] : mu == 1 ? G.stride[1] : mu == 2 ? G.stride[2] : 1u;
+      ssp = (cm > 0 ? s - st : s + (uint32_t)(nm - 1) * st) >> 1;
       par ^= 1;
     }
     off[j] = link_off(copy, par, slot, a.NS, NC, Vh, ssp);
     if (use[j]) {
       load_rows(a.links + off[j], Vh, u[j]);
       reconstruct_row2(u[j]);
-      if (down[j]) dagger(u[j]);
+      if (down) dagger(u[j]);
     } else {
       set_identity(u[j]);
     }
@@ -195,8 +234,41 @@ __global__ void __launch_bounds__(BLOCK) sweep_kernel(const SweepArgs<R> a) {
 #pragma unroll
   for (int j = 0; j < LPT; ++j) {
     if (!use[j]) continue;
-    if (down[j]) dagger(u[j]);
+    const bool down = (LPT >= 2) ? (j & 1) : ((lane * LPT + j) & 1);
+    if (down) dagger(u[j]);
     store_rows(a.links + off[j], Vh, u[j]);
+  }
+}
+
+// Resident blocks per SM requested from the register allocator: FP32 keeps
+// 2-4 blocks of 256 threads per SM (<= 128 / 85 / 64 registers); FP64 with
+// eight or four links per thread needs the whole register file.
+template <typename R, int LPT>
+constexpr int min_blocks() {
+  return sizeof(R) == 4 ? (LPT == 8 ? 1 : LPT == 4 ? 2 : LPT == 2 ? 3 : 4)
+                        : (LPT >= 4 ? 1 : LPT == 2 ? 2 : 3);
+}
+
+template <typename R, int GAUGE, int ALGO, int LPT>
+__global__ void __launch_bounds__(BLOCK, min_blocks<R, LPT>()) sweep_kernel(const SweepArgs<R> a) {
+  constexpr int NC = store_traits<R>::NC;
+  constexpr int L = 8 / LPT;
+  constexpr uint32_t TILE = BLOCK / L;
+  const uint32_t Vh = a.geom.Vh;
+  const uint32_t tiles_per_copy = (Vh + TILE - 1) / TILE;
+  const uint64_t ntiles = (uint64_t)tiles_per_copy * a.ncopies;
+  const int lane = (int)(threadIdx.x % L);
+  const uint32_t local = threadIdx.x / L;
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint64_t next = tile + gridDim.x;
+    if (a.prefetch && next < ntiles && threadIdx.x < 8 * NC) {
+      const uint32_t nc = (uint32_t)(next / tiles_per_copy);
+      const uint32_t nsp0 = (uint32_t)(next - (uint64_t)nc * tiles_per_copy) * TILE;
+      prefetch_tile<R, GAUGE>(a, nc, nsp0, min(TILE, Vh - nsp0), (int)threadIdx.x);
+    }
+    const uint32_t copy = (uint32_t)(tile / tiles_per_copy);
+    const uint32_t sp = (uint32_t)(tile - (uint64_t)copy * tiles_per_copy) * TILE + local;
+    sweep_site<R, GAUGE, ALGO, LPT>(a, copy, sp, sp < Vh, lane);
   }
 }
 

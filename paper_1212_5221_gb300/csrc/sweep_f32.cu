@@ -4,18 +4,43 @@
 
 namespace gfk {
 
+// Persistent grid: as many blocks as fit on the device at once (queried once
+// per kernel instance), each looping over tiles of BLOCK/L sites.
+template <typename K>
+static unsigned resident_blocks(K kernel) {
+  static unsigned cached = 0;
+  if (cached) return cached;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, BLOCK, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  cached = (unsigned)(sms * per_sm);
+  return cached;
+}
+
+template <typename R, int GAUGE, int ALGO, int LPT>
+static cudaError_t launch_one(const SweepArgs<R>& a, cudaStream_t st) {
+  constexpr uint32_t TILE = BLOCK / (8 / LPT);
+  const uint64_t ntiles = (uint64_t)((a.geom.Vh + TILE - 1) / TILE) * a.ncopies;
+  auto kernel = sweep_kernel<R, GAUGE, ALGO, LPT>;
+  const unsigned resident = resident_blocks(kernel);
+  const unsigned blocks = (unsigned)((resident && ntiles > resident) ? resident : ntiles);
+  kernel<<<blocks, BLOCK, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename R, int GAUGE, int ALGO>
 static cudaError_t launch_lpt(const SweepArgs<R>& a, int lpt, cudaStream_t st) {
-  const uint64_t threads = (uint64_t)a.ncopies * a.geom.Vh * (uint64_t)(8 / lpt);
-  const unsigned blocks = (unsigned)((threads + BLOCK - 1) / BLOCK);
   switch (lpt) {
-    case 1: sweep_kernel<R, GAUGE, ALGO, 1><<<blocks, BLOCK, 0, st>>>(a); break;
-    case 2: sweep_kernel<R, GAUGE, ALGO, 2><<<blocks, BLOCK, 0, st>>>(a); break;
-    case 4: sweep_kernel<R, GAUGE, ALGO, 4><<<blocks, BLOCK, 0, st>>>(a); break;
-    case 8: sweep_kernel<R, GAUGE, ALGO, 8><<<blocks, BLOCK, 0, st>>>(a); break;
-    default: return cudaErrorInvalidValue;
+    case 1: return launch_one<R, GAUGE, ALGO, 1>(a, st);
+    case 2: return launch_one<R, GAUGE, ALGO, 2>(a, st);
+    case 4: return launch_one<R, GAUGE, ALGO, 4>(a, st);
+    case 8: return launch_one<R, GAUGE, ALGO, 8>(a, st);
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 template <typename R, int GAUGE>

@@ -80,6 +80,7 @@ _SIG = {
     "gf_set_sweep_index": [_P, ctypes.c_uint64],
     "gf_set_copy_base": [_P, ctypes.c_uint32],
     "gf_set_links_per_thread": [_P, _I],
+    "gf_set_prefetch": [_P, _I],
     "gf_get_links_per_thread": [_P, _PI],
     "gf_autotune": [_P, _I, _PI, _PD],
     "gf_fix": [_P, ctypes.POINTER(gf_fix_params), ctypes.POINTER(gf_fix_result)],
@@ -275,6 +276,10 @@ def gf_set_copy_base(h, base):
 
 def gf_set_links_per_thread(h, lpt):
     _check(lib().gf_set_links_per_thread(h, int(lpt)), "gf_set_links_per_thread")
+
+
+def gf_set_prefetch(h, on=True):
+    _check(lib().gf_set_prefetch(h, 1 if on else 0), "gf_set_prefetch")
 
 
 def gf_get_links_per_thread(h):
