@@ -45,10 +45,15 @@ typedef struct gf_ctx gf_ctx;
  * maximally Abelian gauge of Eq. MAG_functional. */
 typedef enum { GF_LANDAU = 0, GF_COULOMB = 1, GF_MAG = 2 } gf_gauge;
 
-/* Storage/arithmetic precision.  GF_MIXED stores links in FP32 (12 reals,
- * Sec. 4.2) for the bulk of the sweeps and switches to FP64 storage for the
- * final sweeps (see gf_promote / gf_fix); reductions and re-unitarisation are
- * always FP64.  GF_MIXED is not the paper's "MP" (Sec. 4.5). */
+/* Storage/arithmetic precision.  GF_MIXED keeps an FP64 master copy of the
+ * links and runs the bulk of the sweeps on an FP32 working copy (12 reals,
+ * Sec. 4.2) that also accumulates every site's gauge transformation g(x);
+ * the accumulated g, re-unitarised in FP64, is applied to the FP64 master
+ * (U_mu(x) <- g(x) U_mu(x) g(x+mu)^dag) every re-unitarisation interval and
+ * whenever the links are read, and the FP32 copy is re-rounded from it, so
+ * the master never leaves the gauge orbit of the input.  The final sweeps
+ * run on the FP64 master (gf_promote / gf_fix).  Reductions are always FP64.
+ * GF_MIXED is not the paper's "MP" (Sec. 4.5: Step 1 in DP, Step 2 in SP). */
 typedef enum { GF_FP64 = 0, GF_FP32 = 1, GF_MIXED = 2 } gf_precision;
 
 /* Local update (Step 1 of Alg. 1): relaxation (Eq. localsolution per SU(2)
@@ -146,8 +151,9 @@ int gf_functional_theta(gf_ctx* ctx, double* F, double* theta);
 /* Per time-slice F_t and theta_t, arrays of n_copies*Nt (copy-major). */
 int gf_slice_functional_theta(gf_ctx* ctx, double* F_t, double* theta_t);
 
-/* GF_MIXED: switch the storage from FP32 to FP64 (every matrix converted and
- * re-unitarised in FP64).  No-op when the storage is FP64 already. */
+/* GF_MIXED: end the FP32 stage: apply its pending gauge transformation to
+ * the FP64 master and run later sweeps on the master.  No-op when the sweeps
+ * already run in FP64; GF_EINVAL for other precisions. */
 int gf_promote(gf_ctx* ctx);
 
 /* Mark which units take part in sweeps: n_copies*Nt flags (copy-major, one
@@ -182,15 +188,18 @@ int gf_autotune(gf_ctx* ctx, gf_algo algo, int* best_lpt, double* ms_per_sweep_b
  * Coulomb a copy's time-slice) stops as soon as its theta is below target.
  * FP32 storage is re-unitarised every reunit_interval sweeps (Sec. 4.5).
  * GF_MIXED runs FP32 sweeps until every active unit has theta < switch_theta
- * (or theta stops falling), then promotes to FP64 for the final sweeps. */
+ * (or theta has not improved for 25 checks: the FP32 rounding floor), then
+ * promotes to the FP64 master for the final sweeps; a unit counts as
+ * converged only on FP64 links. */
 typedef struct {
   gf_algo algo;          /* GF_OR or GF_RELAX */
   double param;          /* omega */
   double theta_target;   /* e.g. 1e-12 */
   int max_sweeps;        /* per run; GF_ENOTCONV beyond */
   int check_interval;    /* sweeps between theta evaluations, >= 1 */
-  int reunit_interval;   /* FP32 storage: re-unitarise every this many sweeps (0 = never) */
-  double switch_theta;   /* GF_MIXED: FP32 -> FP64 below this theta (e.g. 1e-8) */
+  int reunit_interval;   /* FP32 sweeps: every this many sweeps re-unitarise (GF_FP32) or apply the
+                            accumulated transformation to the FP64 master (GF_MIXED); 0 = never */
+  double switch_theta;   /* GF_MIXED: FP32 -> FP64 sweeps below this theta (e.g. 1e-8) */
   uint64_t seed;         /* unused by OR/RELAX; kept for symmetry with gf_sweep */
 } gf_fix_params;
 

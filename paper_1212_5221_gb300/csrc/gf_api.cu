@@ -84,10 +84,12 @@ Geom make_geom(const int dims[4]) {
 Layout make_layout(const int dims[4], int ncopies, int gauge, int prec) {
   Geom G = make_geom(dims);
   Layout L;
-  const int NS = gauge == GF_COULOMB ? 5 : 4;
-  const size_t mats = (size_t)ncopies * 2 * NS * G.Vh;
-  if (prec != GF_FP64) L.links32 = round_up(mats * 3 * sizeof(float4));
-  if (prec != GF_FP32) L.links64 = round_up(mats * 6 * sizeof(double2));
+  // slot 4: Coulomb's accumulated time-slice transformation, and in GF_MIXED the
+  // FP32 sweeps' accumulated transformation awaiting the FP64 master
+  const int NS32 = (gauge == GF_COULOMB || prec == GF_MIXED) ? 5 : 4;
+  const int NS64 = gauge == GF_COULOMB ? 5 : 4;
+  if (prec != GF_FP64) L.links32 = round_up((size_t)ncopies * 2 * NS32 * G.Vh * 3 * sizeof(float4));
+  if (prec != GF_FP32) L.links64 = round_up((size_t)ncopies * 2 * NS64 * G.Vh * 6 * sizeof(double2));
   L.active = round_up((size_t)ncopies * dims[0] * sizeof(int));
   L.partial = round_up(gfk::observables_partial_doubles(G, ncopies) * sizeof(double));
   L.obs = round_up((size_t)ncopies * dims[0] * 2 * sizeof(double));
@@ -104,7 +106,8 @@ void gfk::set_last_error(const char* msg) { g_last_error = msg; }
 
 struct gf_ctx {
   int dims[4];
-  int ncopies, gauge, prec, NS;
+  int ncopies, gauge, prec;
+  int NS32, NS64;  // slots per site in the FP32 / FP64 arrays
   Geom G;
   Layout layout;
   cudaStream_t st = nullptr;
@@ -116,7 +119,8 @@ struct gf_ctx {
   double* partial = nullptr;
   double* obs_d = nullptr;
   double* staging = nullptr;
-  bool fp64 = false;  // current storage
+  bool fp64 = false;   // storage the sweeps run on
+  bool dirty = false;  // GF_MIXED: FP32 sweeps not yet applied to the FP64 master
   bool all_active = true;
   std::vector<int> active_h;
   uint64_t sweep_index = 0;
@@ -136,9 +140,11 @@ struct gf_ctx {
   double prof_ms[GF_KERNEL_KINDS] = {0};
 
   void* links() const { return fp64 ? links64 : links32; }
-  size_t copy_block_bytes() const {
-    return (size_t)2 * NS * G.Vh * (fp64 ? 6 : 3) * 16;
-  }
+  int NS() const { return fp64 ? NS64 : NS32; }
+  // the array that holds the authoritative links: the FP64 master in GF_MIXED
+  bool master64() const { return prec == GF_MIXED || fp64; }
+  size_t copy_block_bytes(bool f64) const { return (size_t)2 * (f64 ? NS64 : NS32) * G.Vh * (f64 ? 6 : 3) * 16; }
+  size_t copy_block_bytes() const { return copy_block_bytes(fp64); }
 };
 
 namespace {
@@ -196,7 +202,7 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     gfk::SweepArgs<double> a;
     a.links = static_cast<double2*>(c->links64);
     a.geom = c->G;
-    a.NS = c->NS;
+    a.NS = c->NS();
     a.parity = parity;
     a.ncopies = (uint32_t)c->ncopies;
     a.copy0 = c->copy_base;
@@ -206,6 +212,7 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     a.k1 = (uint32_t)(seed >> 32);
     a.sweep = sweep;
     a.prefetch = c->prefetch;
+    a.acc = (c->prec == GF_MIXED && !c->fp64 && c->gauge != GF_COULOMB) ? 1 : 0;
     cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<double>(a, c->gauge, kalgo, lpt, c->st);
     prof_end(c, t0, GF_KERNEL_SWEEP_FP64);
@@ -214,7 +221,7 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     gfk::SweepArgs<float> a;
     a.links = static_cast<float4*>(c->links32);
     a.geom = c->G;
-    a.NS = c->NS;
+    a.NS = c->NS();
     a.parity = parity;
     a.ncopies = (uint32_t)c->ncopies;
     a.copy0 = c->copy_base;
@@ -224,6 +231,7 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     a.k1 = (uint32_t)(seed >> 32);
     a.sweep = sweep;
     a.prefetch = c->prefetch;
+    a.acc = (c->prec == GF_MIXED && !c->fp64 && c->gauge != GF_COULOMB) ? 1 : 0;
     cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<float>(a, c->gauge, kalgo, lpt, c->st);
     prof_end(c, t0, GF_KERNEL_SWEEP_FP32);
@@ -241,16 +249,17 @@ int full_sweep(gf_ctx* c, int kalgo, int api_algo, double param, uint64_t seed, 
     int r = launch_half(c, kalgo, param, p, seed, sw, lpt);
     if (r) return r;
   }
+  if (c->prec == GF_MIXED && !c->fp64) c->dirty = true;
   c->sweep_index++;
   return GF_OK;
 }
 
-int observables(gf_ctx* c, std::vector<double>& per_ct) {
+int observables_on(gf_ctx* c, std::vector<double>& per_ct, bool f64) {
   cudaEvent_t t0 = prof_begin(c);
-  cudaError_t e = c->fp64 ? gfk::launch_observables<double>(c->links64, c->G, c->NS, c->gauge, c->ncopies,
-                                                             c->partial, c->obs_d, c->st)
-                          : gfk::launch_observables<float>(c->links32, c->G, c->NS, c->gauge, c->ncopies,
-                                                            c->partial, c->obs_d, c->st);
+  cudaError_t e = f64 ? gfk::launch_observables<double>(c->links64, c->G, c->NS64, c->gauge, c->ncopies,
+                                                         c->partial, c->obs_d, c->st)
+                      : gfk::launch_observables<float>(c->links32, c->G, c->NS32, c->gauge, c->ncopies,
+                                                        c->partial, c->obs_d, c->st);
   if (e != cudaSuccess) return fail(GF_ECUDA, "observables launch: %s", cudaGetErrorString(e));
   prof_end(c, t0, GF_KERNEL_OBSERVABLES);
   c->launch_count += 2;
@@ -261,6 +270,9 @@ int observables(gf_ctx* c, std::vector<double>& per_ct) {
   prof_collect(c);
   return GF_OK;
 }
+
+// observables of the storage the sweeps run on
+int observables(gf_ctx* c, std::vector<double>& per_ct) { return observables_on(c, per_ct, c->fp64); }
 
 void copy_means(const gf_ctx* c, const std::vector<double>& ct, double* F, double* T) {
   const int Nt = c->dims[0];
@@ -283,23 +295,61 @@ int upload_active(gf_ctx* c) {
   return GF_OK;
 }
 
-int coulomb_fold(gf_ctx* c) {
+int coulomb_fold(gf_ctx* c, bool f64) {
   if (c->gauge != GF_COULOMB) return GF_OK;
-  cudaError_t e = c->fp64 ? gfk::launch_coulomb_fold<double>(c->links64, c->G, c->ncopies, c->st)
-                          : gfk::launch_coulomb_fold<float>(c->links32, c->G, c->ncopies, c->st);
+  cudaError_t e = f64 ? gfk::launch_coulomb_fold<double>(c->links64, c->G, c->ncopies, c->st)
+                      : gfk::launch_coulomb_fold<float>(c->links32, c->G, c->ncopies, c->st);
   if (e != cudaSuccess) return fail(GF_ECUDA, "coulomb fold: %s", cudaGetErrorString(e));
   c->launch_count += 2;
   return GF_OK;
 }
 
+// Identity in slots [first, last] of every array the context holds.
 int set_identity_slots(gf_ctx* c, int first, int last) {
-  for (int s = first; s <= last; ++s) {
-    cudaError_t e = c->fp64 ? gfk::launch_identity_slot<double>(c->links64, c->G, c->NS, s, c->ncopies, c->st)
-                            : gfk::launch_identity_slot<float>(c->links32, c->G, c->NS, s, c->ncopies, c->st);
-    if (e != cudaSuccess) return fail(GF_ECUDA, "identity: %s", cudaGetErrorString(e));
-    c->launch_count++;
+  for (int f64 = 0; f64 < 2; ++f64) {
+    void* l = f64 ? c->links64 : c->links32;
+    const int ns = f64 ? c->NS64 : c->NS32;
+    if (!l) continue;
+    for (int s = first; s <= last && s < ns; ++s) {
+      cudaError_t e = f64 ? gfk::launch_identity_slot<double>(l, c->G, ns, s, c->ncopies, c->st)
+                          : gfk::launch_identity_slot<float>(l, c->G, ns, s, c->ncopies, c->st);
+      if (e != cudaSuccess) return fail(GF_ECUDA, "identity: %s", cudaGetErrorString(e));
+      c->launch_count++;
+    }
   }
   return GF_OK;
+}
+
+// GF_MIXED: apply the FP32 sweeps' accumulated transformation to the FP64
+// master and re-round the FP32 copy from it.
+int sync_master(gf_ctx* c) {
+  if (c->prec != GF_MIXED || c->fp64 || !c->dirty) return GF_OK;
+  cudaEvent_t t0 = prof_begin(c);
+  cudaError_t e = gfk::launch_sync_master(c->links32, c->links64, c->G, c->NS32, c->NS64, c->ncopies, c->st);
+  if (e != cudaSuccess) return fail(GF_ECUDA, "sync: %s", cudaGetErrorString(e));
+  prof_end(c, t0, GF_KERNEL_OTHER);
+  c->launch_count += 2;
+  c->dirty = false;
+  return GF_OK;
+}
+
+// GF_MIXED: restart the FP32 copy from the FP64 master (accumulator = 1).
+int refresh32(gf_ctx* c) {
+  if (c->prec != GF_MIXED) return GF_OK;
+  cudaError_t e = gfk::launch_demote(c->links64, c->links32, c->G, c->NS64, c->NS32, c->ncopies, c->st);
+  if (e != cudaSuccess) return fail(GF_ECUDA, "demote: %s", cudaGetErrorString(e));
+  c->launch_count += 2;
+  c->fp64 = false;
+  c->dirty = false;
+  return GF_OK;
+}
+
+// Bring the master up to date: pending FP32 transformation applied, and for
+// Coulomb the accumulated slice transformation folded into U_0.
+int consolidate(gf_ctx* c) {
+  int r = sync_master(c);
+  if (r) return r;
+  return coulomb_fold(c, c->master64());
 }
 
 int create_impl(const int dims[4], int ncopies, int gauge, int prec, void* stream, void* buf, size_t bytes,
@@ -319,7 +369,8 @@ int create_impl(const int dims[4], int ncopies, int gauge, int prec, void* strea
   c->ncopies = ncopies;
   c->gauge = gauge;
   c->prec = prec;
-  c->NS = gauge == GF_COULOMB ? 5 : 4;
+  c->NS32 = (gauge == GF_COULOMB || prec == GF_MIXED) ? 5 : 4;
+  c->NS64 = gauge == GF_COULOMB ? 5 : 4;
   c->G = make_geom(dims);
   c->layout = make_layout(dims, ncopies, gauge, prec);
   c->fp64 = prec == GF_FP64;
@@ -363,7 +414,7 @@ int create_impl(const int dims[4], int ncopies, int gauge, int prec, void* strea
   c->obs_d = reinterpret_cast<double*>(base + off); off += L.obs;
   c->staging = reinterpret_cast<double*>(base + off); off += L.staging;
   r = upload_active(c);
-  if (!r) r = set_identity_slots(c, 0, c->NS - 1);
+  if (!r) r = set_identity_slots(c, 0, 4);
   if (!r) {
     cudaError_t e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) r = fail(GF_ECUDA, "init: %s", cudaGetErrorString(e));
@@ -385,32 +436,38 @@ int check_copy(gf_ctx* c, int copy, bool allow_all) {
 }
 
 // Import time-slices [t0, t0+nt) of copy `copy` from natural-order doubles on the device.
+// Layout conversion into / out of the master array.
 int import_slab(gf_ctx* c, int copy, int t0, int nt, const double* dev) {
-  cudaError_t e = c->fp64 ? gfk::launch_import<double>(dev, c->links64, c->G, c->NS, copy, t0, nt, c->st)
-                          : gfk::launch_import<float>(dev, c->links32, c->G, c->NS, copy, t0, nt, c->st);
+  cudaError_t e = c->master64() ? gfk::launch_import<double>(dev, c->links64, c->G, c->NS64, copy, t0, nt, c->st)
+                                : gfk::launch_import<float>(dev, c->links32, c->G, c->NS32, copy, t0, nt, c->st);
   if (e != cudaSuccess) return fail(GF_ECUDA, "import: %s", cudaGetErrorString(e));
   c->launch_count++;
   return GF_OK;
 }
 
 int export_slab(gf_ctx* c, int copy, int t0, int nt, double* dev) {
-  cudaError_t e = c->fp64 ? gfk::launch_export<double>(dev, c->links64, c->G, c->NS, copy, t0, nt, c->st)
-                          : gfk::launch_export<float>(dev, c->links32, c->G, c->NS, copy, t0, nt, c->st);
+  cudaError_t e = c->master64() ? gfk::launch_export<double>(dev, c->links64, c->G, c->NS64, copy, t0, nt, c->st)
+                                : gfk::launch_export<float>(dev, c->links32, c->G, c->NS32, copy, t0, nt, c->st);
   if (e != cudaSuccess) return fail(GF_ECUDA, "export: %s", cudaGetErrorString(e));
   c->launch_count++;
   return GF_OK;
 }
 
-// A new problem: MIXED returns to FP32 storage; Coulomb's accumulated g = 1.
+// A new problem: links go to the master array; pending transformations are
+// dropped (slot 4 = 1 in every array).
 int begin_load(gf_ctx* c) {
-  if (c->prec == GF_MIXED) c->fp64 = false;
-  if (c->gauge == GF_COULOMB) return set_identity_slots(c, 4, 4);
+  c->dirty = false;
+  if (c->prec == GF_MIXED || c->gauge == GF_COULOMB) return set_identity_slots(c, 4, 4);
   return GF_OK;
 }
 
+// After new links reached the master: GF_MIXED restarts its FP32 copy.
+int end_load(gf_ctx* c) { return refresh32(c); }
+
 int replicate_copy0(gf_ctx* c) {
-  const size_t blk = c->copy_block_bytes();
-  char* base = static_cast<char*>(c->links());
+  const bool f64 = c->master64();
+  const size_t blk = c->copy_block_bytes(f64);
+  char* base = static_cast<char*>(f64 ? c->links64 : c->links32);
   for (int k = 1; k < c->ncopies; ++k)
     GF_CUDA(cudaMemcpyAsync(base + k * blk, base, blk, cudaMemcpyDeviceToDevice, c->st));
   return GF_OK;
@@ -450,8 +507,30 @@ int api_sweep(gf_ctx* c, int algo, double param, uint64_t seed) {
   return fail(GF_EINVAL, "bad algorithm %d", algo);
 }
 
+// End of a public sweep call: the master is brought up to date (GF_MIXED) and
+// the exact observables of the master are returned if asked for.
+int finish_public(gf_ctx* c, double* F, double* theta) {
+  int r = sync_master(c);
+  if (r) return r;
+  if (F || theta) {
+    std::vector<double> ct;
+    if ((r = observables_on(c, ct, c->master64()))) return r;
+    copy_means(c, ct, F, theta);
+    return GF_OK;
+  }
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  return GF_OK;
+}
+
 int reunitarize(gf_ctx* c) {
-  const uint64_t nmat = (uint64_t)c->ncopies * 2 * c->NS * c->G.Vh;
+  // GF_MIXED with FP32 sweeps: the FP64 master stays unitary; re-rounding the
+  // FP32 copy from it (after applying the pending transformation) replaces the
+  // re-unitarisation of the FP32 links.
+  if (c->prec == GF_MIXED && !c->fp64) {
+    c->dirty = true;
+    return sync_master(c);
+  }
+  const uint64_t nmat = (uint64_t)c->ncopies * 2 * c->NS() * c->G.Vh;
   cudaEvent_t t0 = prof_begin(c);
   cudaError_t e = c->fp64 ? gfk::launch_reunitarize<double>(c->links64, c->G.Vh, nmat, c->st)
                           : gfk::launch_reunitarize<float>(c->links32, c->G.Vh, nmat, c->st);
@@ -461,15 +540,13 @@ int reunitarize(gf_ctx* c) {
   return GF_OK;
 }
 
+// GF_MIXED: switch the sweeps to the FP64 master (the FP32 stage's pending
+// transformation applied first).
 int promote(gf_ctx* c) {
   if (c->fp64) return GF_OK;
   if (c->prec != GF_MIXED) return fail(GF_EINVAL, "gf_promote needs a GF_MIXED context");
-  const uint64_t nmat = (uint64_t)c->ncopies * 2 * c->NS * c->G.Vh;
-  cudaEvent_t t0 = prof_begin(c);
-  cudaError_t e = gfk::launch_promote(c->links32, c->links64, c->G.Vh, nmat, c->st);
-  if (e != cudaSuccess) return fail(GF_ECUDA, "promote: %s", cudaGetErrorString(e));
-  prof_end(c, t0, GF_KERNEL_OTHER);
-  c->launch_count++;
+  int r = sync_master(c);
+  if (r) return r;
   c->fp64 = true;
   return GF_OK;
 }
@@ -527,6 +604,7 @@ int gf_load_links_slab(gf_ctx* c, int copy, int t0, int nt, const double* host) 
     if ((r = import_slab(c, dst, t, n, c->staging))) return r;
   }
   if (copy < 0 && (r = replicate_copy0(c))) return r;
+  if ((r = end_load(c))) return r;
   GF_CUDA(cudaStreamSynchronize(c->st));
   return GF_OK;
 }
@@ -545,6 +623,7 @@ int gf_load_links_device(gf_ctx* c, int copy, const double* dev) {
   if ((r = begin_load(c))) return r;
   if ((r = import_slab(c, copy < 0 ? 0 : copy, 0, c->dims[0], dev))) return r;
   if (copy < 0 && (r = replicate_copy0(c))) return r;
+  if ((r = end_load(c))) return r;
   GF_CUDA(cudaStreamSynchronize(c->st));
   return GF_OK;
 }
@@ -554,7 +633,7 @@ int gf_store_links(gf_ctx* c, int copy, double* host) {
   if (r) return r;
   if ((r = check_copy(c, copy, false))) return r;
   if (!host) return fail(GF_EINVAL, "host is NULL");
-  if ((r = coulomb_fold(c))) return r;
+  if ((r = consolidate(c))) return r;
   const size_t per_t = (size_t)c->G.V3 * 4 * 18;
   for (int t = 0; t < c->dims[0]; t += c->layout.slab_nt) {
     const int n = std::min(c->layout.slab_nt, c->dims[0] - t);
@@ -571,7 +650,7 @@ int gf_store_links_device(gf_ctx* c, int copy, double* dev) {
   if (r) return r;
   if ((r = check_copy(c, copy, false))) return r;
   if (!dev) return fail(GF_EINVAL, "device_dst is NULL");
-  if ((r = coulomb_fold(c))) return r;
+  if ((r = consolidate(c))) return r;
   if ((r = export_slab(c, copy, 0, c->dims[0], dev))) return r;
   GF_CUDA(cudaStreamSynchronize(c->st));
   return GF_OK;
@@ -580,11 +659,13 @@ int gf_store_links_device(gf_ctx* c, int copy, double* dev) {
 int gf_random_gauge_transform(gf_ctx* c, uint64_t seed) {
   int r = check_ctx(c);
   if (r) return r;
-  if ((r = coulomb_fold(c))) return r;
-  cudaError_t e = c->fp64 ? gfk::launch_haar_transform<double>(c->links64, c->G, c->NS, c->ncopies, c->copy_base, seed, c->st)
-                          : gfk::launch_haar_transform<float>(c->links32, c->G, c->NS, c->ncopies, c->copy_base, seed, c->st);
+  if ((r = consolidate(c))) return r;
+  cudaError_t e = c->master64()
+                      ? gfk::launch_haar_transform<double>(c->links64, c->G, c->NS64, c->ncopies, c->copy_base, seed, c->st)
+                      : gfk::launch_haar_transform<float>(c->links32, c->G, c->NS32, c->ncopies, c->copy_base, seed, c->st);
   if (e != cudaSuccess) return fail(GF_ECUDA, "random gauge transform: %s", cudaGetErrorString(e));
   c->launch_count += 2;
+  if ((r = refresh32(c))) return r;
   GF_CUDA(cudaStreamSynchronize(c->st));
   return GF_OK;
 }
@@ -596,14 +677,7 @@ int gf_sweep(gf_ctx* c, gf_algo algo, double param, int n_sweeps, uint64_t seed,
   if (n_sweeps < 0) return fail(GF_EINVAL, "n_sweeps < 0");
   for (int k = 0; k < n_sweeps; ++k)
     if ((r = api_sweep(c, algo, param, seed))) return r;
-  if (F || theta) {
-    std::vector<double> ct;
-    if ((r = observables(c, ct))) return r;
-    copy_means(c, ct, F, theta);
-  } else {
-    GF_CUDA(cudaStreamSynchronize(c->st));
-  }
-  return GF_OK;
+  return finish_public(c, F, theta);
 }
 
 int gf_anneal(gf_ctx* c, double T0, double T1, int n_steps, uint64_t seed, double* F, double* theta) {
@@ -616,14 +690,7 @@ int gf_anneal(gf_ctx* c, double T0, double T1, int n_steps, uint64_t seed, doubl
     const double T = n_steps > 1 ? T0 + (T1 - T0) * (double)k / (double)(n_steps - 1) : T0;
     if ((r = api_sweep(c, GF_SA, T, seed))) return r;
   }
-  if (F || theta) {
-    std::vector<double> ct;
-    if ((r = observables(c, ct))) return r;
-    copy_means(c, ct, F, theta);
-  } else {
-    GF_CUDA(cudaStreamSynchronize(c->st));
-  }
-  return GF_OK;
+  return finish_public(c, F, theta);
 }
 
 int gf_reunitarize(gf_ctx* c) {
@@ -637,8 +704,9 @@ int gf_reunitarize(gf_ctx* c) {
 int gf_functional_theta(gf_ctx* c, double* F, double* theta) {
   int r = check_ctx(c);
   if (r) return r;
+  if ((r = sync_master(c))) return r;
   std::vector<double> ct;
-  if ((r = observables(c, ct))) return r;
+  if ((r = observables_on(c, ct, c->master64()))) return r;
   copy_means(c, ct, F, theta);
   return GF_OK;
 }
@@ -646,8 +714,9 @@ int gf_functional_theta(gf_ctx* c, double* F, double* theta) {
 int gf_slice_functional_theta(gf_ctx* c, double* F_t, double* theta_t) {
   int r = check_ctx(c);
   if (r) return r;
+  if ((r = sync_master(c))) return r;
   std::vector<double> ct;
-  if ((r = observables(c, ct))) return r;
+  if ((r = observables_on(c, ct, c->master64()))) return r;
   for (size_t k = 0; k < ct.size() / 2; ++k) {
     if (F_t) F_t[k] = ct[2 * k];
     if (theta_t) theta_t[k] = ct[2 * k + 1];

@@ -44,12 +44,6 @@ cudaError_t launch_reunitarize(void* links, uint32_t Vh, uint64_t nmat, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_promote(const void* src32, void* dst64, uint32_t Vh, uint64_t nmat, cudaStream_t st) {
-  promote_kernel<<<nblocks(nmat), BLOCK, 0, st>>>(static_cast<const float4*>(src32),
-                                                   static_cast<double2*>(dst64), Vh, nmat);
-  return cudaGetLastError();
-}
-
 template <typename R>
 cudaError_t launch_import(const double* nat, void* links, const Geom& G, int NS, uint32_t copy, uint32_t t0,
                           uint32_t nt, cudaStream_t st) {
@@ -105,6 +99,26 @@ cudaError_t launch_philox(const void* ctr, void* out, uint64_t n, uint64_t seed,
   philox_kernel<<<nblocks(n), BLOCK, 0, st>>>(static_cast<const uint4*>(ctr), static_cast<uint4*>(out), n,
                                               (uint32_t)seed, (uint32_t)(seed >> 32));
   return cudaGetLastError();
+}
+
+cudaError_t launch_sync_master(void* l32, void* l64, const Geom& G, int NS32, int NS64, uint32_t ncopies,
+                               cudaStream_t st) {
+  const uint64_t n = (uint64_t)ncopies * G.V * 4;
+  sync_master_kernel<<<nblocks(n), BLOCK, 0, st>>>(static_cast<float4*>(l32), static_cast<double2*>(l64), G,
+                                                    NS32, NS64, ncopies);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_identity_slot<float>(l32, G, NS32, 4, ncopies, st);
+}
+
+cudaError_t launch_demote(const void* l64, void* l32, const Geom& G, int NS64, int NS32, uint32_t ncopies,
+                          cudaStream_t st) {
+  const uint64_t n = (uint64_t)ncopies * 2 * 4 * G.Vh;
+  demote_kernel<<<nblocks(n), BLOCK, 0, st>>>(static_cast<const double2*>(l64), static_cast<float4*>(l32), G.Vh,
+                                               NS64, NS32, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_identity_slot<float>(l32, G, NS32, 4, ncopies, st);
 }
 
 #define GF_INST(R)                                                                                         \

@@ -183,23 +183,6 @@ __global__ void __launch_bounds__(BLOCK) reunitarize_kernel(typename store_trait
   store_rows(p, Vh, u);
 }
 
-// Precision switch: FP32 storage -> FP64 storage, re-unitarised in FP64.
-__global__ void __launch_bounds__(BLOCK) promote_kernel(const float4* src, double2* dst, uint32_t Vh,
-                                                        uint64_t nmat) {
-  const uint64_t m = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
-  if (m >= nmat) return;
-  const uint64_t blk = m / Vh, sp = m - blk * Vh;
-  mat3<float> u;
-  load_rows(src + blk * 3 * Vh + sp, Vh, u);
-  mat3<double> d;
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) d.e[a][b] = {(double)u.e[a][b].re, (double)u.e[a][b].im};
-  gram_schmidt_rows(d);
-  store_rows(dst + blk * 6 * Vh + sp, Vh, d);
-}
-
 // ---------------------------------------------------------------------------
 // Layout conversion between the natural order (t,x,y,z,mu,i,j,re/im; 18
 // doubles per link) and the parity-split storage, for the time-slices
@@ -387,4 +370,94 @@ __global__ void philox_kernel(const uint4* ctr, uint4* out, uint64_t n, uint32_t
   out[i] = make_uint4(r.x, r.y, r.z, r.w);
 }
 
+// ---------------------------------------------------------------------------
+// Mixed precision, FP64 master: apply the gauge transformation accumulated by
+// the FP32 sweeps (slot 4 of the FP32 array) to the FP64 links,
+// U_mu(x) <- G(x) U_mu(x) G(x+mu)^dag in FP64 with G re-unitarised in FP64,
+// and write the result back to both arrays (the FP32 copy re-rounded from the
+// exact one).  One thread per (site, mu).  The accumulator is reset by a
+// separate launch once every thread has read it.
+__device__ __forceinline__ void load_g_fp64(const float4* l32, uint32_t copy, int p, int NS32, uint32_t Vh,
+                                            uint32_t sp, mat3<double>& g) {
+  mat3<float> f;
+  load_rows(l32 + link_off(copy, p, 4, NS32, 3, Vh, sp), Vh, f);
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) g.e[a][b] = {(double)f.e[a][b].re, (double)f.e[a][b].im};
+  gram_schmidt_rows(g);
+  reconstruct_row2(g);
+}
+
+__global__ void __launch_bounds__(BLOCK) sync_master_kernel(float4* l32, double2* l64, Geom G, int NS32, int NS64,
+                                                            uint32_t ncopies) {
+  const uint64_t tid = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  const uint64_t per_copy = (uint64_t)G.V * 4;
+  const uint32_t copy = (uint32_t)(tid / per_copy);
+  if (copy >= ncopies) return;
+  const uint32_t r = (uint32_t)(tid - (uint64_t)copy * per_copy);
+  const int mu = (int)(r & 3);
+  const uint32_t site = r >> 2;  // 0 .. V-1 over both parities
+  const int p = site >= G.Vh;
+  const uint32_t sp = site - (p ? G.Vh : 0);
+  int c[4];
+  uint32_t s;
+  site_coords(G, sp, p, c, s);
+  mat3<double> gx, gy, u, t;
+  load_g_fp64(l32, copy, p, NS32, G.Vh, sp, gx);
+  load_g_fp64(l32, copy, p ^ 1, NS32, G.Vh, site_plus(G, s, c, mu) >> 1, gy);
+  const size_t off64 = link_off(copy, p, mu, NS64, 6, G.Vh, sp);
+  load_rows(l64 + off64, G.Vh, u);
+  reconstruct_row2(u);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      cx<double> acc{0.0, 0.0};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        cx<double> v = cmul(gx.e[a][q], u.e[q][b]);
+        acc.re += v.re;
+        acc.im += v.im;
+      }
+      t.e[a][b] = acc;
+    }
+  mat3<float> f;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      cx<double> acc{0.0, 0.0};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        cx<double> v = cmul(t.e[a][q], cx<double>{gy.e[b][q].re, -gy.e[b][q].im});
+        acc.re += v.re;
+        acc.im += v.im;
+      }
+      u.e[a][b] = acc;
+      f.e[a][b] = {(float)acc.re, (float)acc.im};
+    }
+  store_rows(l64 + off64, G.Vh, u);
+  store_rows(l32 + link_off(copy, p, mu, NS32, 3, G.Vh, sp), G.Vh, f);
+}
+
+// FP32 copy <- FP64 master (links only), for a fresh start of the FP32 sweeps.
+__global__ void __launch_bounds__(BLOCK) demote_kernel(const double2* l64, float4* l32, uint32_t Vh, int NS64,
+                                                       int NS32, uint64_t nlinks) {
+  const uint64_t m = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (m >= nlinks) return;
+  const uint64_t sp = m % Vh;
+  const uint64_t rest = m / Vh;  // (copy*2 + p)*4 + mu
+  const uint64_t mu = rest & 3, cp = rest >> 2;
+  mat3<double> d;
+  load_rows(l64 + ((cp * NS64 + mu) * 6) * Vh + sp, Vh, d);
+  mat3<float> f;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) f.e[a][b] = {(float)d.e[a][b].re, (float)d.e[a][b].im};
+  store_rows(l32 + ((cp * NS32 + mu) * 3) * Vh + sp, Vh, f);
+}
+
 }  // namespace gfk
+

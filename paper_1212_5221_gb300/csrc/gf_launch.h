@@ -21,7 +21,6 @@ size_t observables_partial_doubles(const Geom& G, uint32_t ncopies);
 
 template <typename R>
 cudaError_t launch_reunitarize(void* links, uint32_t Vh, uint64_t nmat, cudaStream_t st);
-cudaError_t launch_promote(const void* src32, void* dst64, uint32_t Vh, uint64_t nmat, cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_import(const double* nat, void* links, const Geom& G, int NS, uint32_t copy, uint32_t t0,
@@ -40,6 +39,14 @@ cudaError_t launch_coulomb_fold(void* links, const Geom& G, uint32_t ncopies, cu
 template <typename R>
 cudaError_t launch_identity_slot(void* links, const Geom& G, int NS, int slot, uint32_t ncopies,
                                  cudaStream_t st);
+
+// Mixed precision with an FP64 master: apply the FP32-accumulated gauge
+// transformation (slot 4) to the FP64 links and re-round the FP32 copy, then
+// reset the accumulator; and the plain FP64 -> FP32 copy (accumulator = 1).
+cudaError_t launch_sync_master(void* l32, void* l64, const Geom& G, int NS32, int NS64, uint32_t ncopies,
+                               cudaStream_t st);
+cudaError_t launch_demote(const void* l64, void* l32, const Geom& G, int NS64, int NS32, uint32_t ncopies,
+                          cudaStream_t st);
 
 // Record the calling thread's error message (read by gf_last_error).
 void set_last_error(const char* msg);

@@ -21,6 +21,8 @@ struct SweepArgs {
   uint32_t k0, k1;    // Philox key (the seed)
   uint32_t sweep;     // sweep index for the random draws
   int prefetch;       // 1: prefetch the next tile into L2
+  int acc;            // 1: slot 4 accumulates g(x) (mixed precision; never for Coulomb,
+                      //    whose slot 0 already does)
 };
 
 // Element offset of (copy, parity, slot, chunk 0, site index).
@@ -160,6 +162,20 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
     }
   }
 
+  // mixed precision: the accumulated gauge transformation of this site
+  mat3<R> gacc;
+  size_t acc_off = 0;
+  const bool use_acc = a.acc && valid && lane == 0;
+  if (a.acc) {
+    if (use_acc) {
+      acc_off = link_off(copy, a.parity, 4, a.NS, NC, Vh, sp);
+      load_rows(a.links + acc_off, Vh, gacc);
+      reconstruct_row2(gacc);
+    } else {
+      set_identity(gacc);
+    }
+  }
+
   Rng rng{a.k0, a.k1, s, a.sweep, a.copy0 + copy};
 
 #pragma unroll
@@ -229,7 +245,9 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
     }
 #pragma unroll
     for (int j = 0; j < LPT; ++j) left_subgroup_mult(u[j], i, j2, g);
+    if (a.acc) left_subgroup_mult(gacc, i, j2, g);
   }
+  if (use_acc) store_rows(a.links + acc_off, Vh, gacc);
 
 #pragma unroll
   for (int j = 0; j < LPT; ++j) {
