@@ -297,19 +297,33 @@ def run_ours(args, rank, world, local_rank):
     if stats[1][0]:
         sweep64_gbs = BYTES_PER_SU["fp64"] * sites_per_launch / (stats[1][1] / stats[1][0] / 1e3) / 1e9
 
+    # the FP32 sweep kernel's own roofline (HBM), from the same timed steps
+    roof32 = None
+    if stats[0][0]:
+        a32 = BYTES_PER_SU["fp32"] * sites_per_launch / (stats[0][1] / stats[0][0] / 1e3) / 1e9
+        roof32 = {"bound": "hbm", "achieved": a32, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                  "frac": a32 / peaks["hbm_gbs"], "traffic": ncu_traffic("sweep_fp32"),
+                  "avg_launch_ms": stats[0][1] / stats[0][0]}
+
     out = {}
     if rank == 0:
-        # plain FP64 time-to-theta on the same problem (one run, untimed by the steps)
-        fp64 = None
-        if args.fp64_baseline:
-            f64 = gf.GaugeField(dims, W["gauge"], "fp64", device=dev)
-            gf.gf_load_links_device(f64.h, 0, src.data_ptr())
-            gf.gf_random_gauge_transform(f64.h, 1000)
-            kw = dict(fix_kw)
-            r64 = gf.gf_fix(f64.h, **kw)
-            fp64 = {"seconds": r64["seconds"], "sweeps": r64["sweeps"],
-                    "site_updates_per_s": r64["site_updates"] / r64["seconds"]}
-            f64.close()
+        def one_run(prec, switch):
+            fld = gf.GaugeField(dims, W["gauge"], prec, device=dev)
+            gf.gf_load_links_device(fld.h, 0, src.data_ptr())
+            gf.gf_random_gauge_transform(fld.h, 1000)
+            kw = dict(fix_kw, switch_theta=switch)
+            r = gf.gf_fix(fld.h, **kw)
+            F, T = gf.gf_functional_theta(fld.h)
+            fld.close()
+            return {"seconds": r["seconds"], "sweeps": r["sweeps"], "sweeps_fp32": r["sweeps_fp32"],
+                    "sweeps_fp64": r["sweeps_fp64"], "site_updates_per_s": r["site_updates"] / r["seconds"],
+                    "F": float(F[0]), "theta": float(T[0])}
+
+        # the same problem (orbit seed 1000) as plain FP64, and in mixed precision with the
+        # switch to FP64 sweeps moved down to the FP32 floor (one run each, outside the steps)
+        fp64 = one_run("fp64", args.switch_theta) if args.fp64_baseline else None
+        deep = one_run("mixed", args.deep_switch) if args.deep_switch > 0 else None
+        literal = one_run("mixed", args.switch_theta) if args.fp64_baseline else None
         # end to end through the C ABI with pinned host buffers
         e2e = None
         if args.e2e_steps > 0:
@@ -352,11 +366,20 @@ def run_ours(args, rank, world, local_rank):
                        "then Haar g(x) per step", "l2": "inputs larger than L2 (403 MB FP32 links)",
                        "parallelism": f"replicas x{world}"},
             "time_to_theta_s": {"mixed": mixed_tt, "fp64": fp64["seconds"] if fp64 else None,
-                                "speedup_mixed_vs_fp64": (fp64["seconds"] / mixed_tt) if fp64 else None},
+                                "speedup_mixed_vs_fp64": (fp64["seconds"] / mixed_tt) if fp64 else None,
+                                "mixed_deep_switch": deep["seconds"] if deep else None,
+                                "speedup_mixed_deep_vs_fp64": (fp64["seconds"] / deep["seconds"])
+                                if (fp64 and deep) else None},
+            "same_orbit_runs": {"fp64": fp64, "mixed_switch_1e-8": literal,
+                                f"mixed_switch_{args.deep_switch:g}": deep,
+                                "rel_dF_mixed_vs_fp64": abs(literal["F"] - fp64["F"]) / fp64["F"]
+                                if (fp64 and literal) else None,
+                                "rel_dF_deep_vs_fp64": abs(deep["F"] - fp64["F"]) / fp64["F"]
+                                if (fp64 and deep) else None},
             "sweeps_per_step": {"fp32": sweeps32 / args.steps, "fp64": sweeps64 / args.steps},
             "hbm_gbs": {"sweep_fp32": sweep32_gbs, "sweep_fp64": sweep64_gbs},
-            "fp64_run": fp64,
             "roofline": roof,
+            "roofline_sweep_fp32": roof32,
             "kernel_ms": kernel_ms,
             "gpu_launches": int(launches),
             "e2e": e2e,
@@ -394,6 +417,8 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "fp64", "fp32"], default="mixed")
     ap.add_argument("--switch-theta", type=float, default=WORKLOAD["switch_theta"])
     ap.add_argument("--max-sweeps", type=int, default=40000)
+    ap.add_argument("--deep-switch", type=float, default=1e-13,
+                    help="also time one mixed run with the FP32 -> FP64 switch at this theta (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-fp64-baseline", dest="fp64_baseline", action="store_false")
