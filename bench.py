@@ -43,7 +43,9 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(name="landau_or_32c3x64_mixed", dims=(64, 32, 32, 32), gauge="landau", eps=0.35,
                 field_seed=1, omega=1.7, theta=1e-12, switch_theta=1e-8, reunit=100, check=20)
 METRIC = "site-updates/s & HBM GB/s (mixed vs FP64); time-to-θ<1e-12; job p50/p99"
-BYTES_PER_SU = {"fp32": 768, "fp64": 1536}  # 8 links x 12 reals x (load + store)
+# 8 links x 12 reals x (load + store); the mixed-precision FP32 sweep also reads and
+# writes the site's accumulated gauge transformation (one more 12-real matrix)
+BYTES_PER_SU = {"fp32": 768, "fp64": 1536, "fp32_acc": 864}
 FLOP_PER_SU = 2274  # App. A: 192 gather + 66 OR + 2016 apply
 FP64_PEAK_TFLOPS = 1.25  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal table)
 
@@ -274,7 +276,8 @@ def run_ours(args, rank, world, local_rank):
     avg_s = ms_l / max(n_l, 1) / 1e3
     sites_per_launch = V // 2  # one sublattice
     if dom == 0:
-        roof = {"bound": "hbm", "achieved": BYTES_PER_SU["fp32"] * sites_per_launch / avg_s / 1e9,
+        b32 = BYTES_PER_SU["fp32_acc" if args.precision == "mixed" else "fp32"]
+        roof = {"bound": "hbm", "achieved": b32 * sites_per_launch / avg_s / 1e9,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s"}
         roof["traffic"] = ncu_traffic("sweep_fp32")
     elif dom == 1:
@@ -292,7 +295,8 @@ def run_ours(args, rank, world, local_rank):
     kernel_ms = {kind_names[k]: {"launches": stats[k][0], "ms": round(stats[k][1], 3)} for k in stats}
     sweep32_gbs = None
     if stats[0][0]:
-        sweep32_gbs = BYTES_PER_SU["fp32"] * sites_per_launch / (stats[0][1] / stats[0][0] / 1e3) / 1e9
+        sweep32_gbs = (BYTES_PER_SU["fp32_acc" if args.precision == "mixed" else "fp32"] * sites_per_launch /
+                       (stats[0][1] / stats[0][0] / 1e3) / 1e9)
     sweep64_gbs = None
     if stats[1][0]:
         sweep64_gbs = BYTES_PER_SU["fp64"] * sites_per_launch / (stats[1][1] / stats[1][0] / 1e3) / 1e9
@@ -300,7 +304,8 @@ def run_ours(args, rank, world, local_rank):
     # the FP32 sweep kernel's own roofline (HBM), from the same timed steps
     roof32 = None
     if stats[0][0]:
-        a32 = BYTES_PER_SU["fp32"] * sites_per_launch / (stats[0][1] / stats[0][0] / 1e3) / 1e9
+        b32 = BYTES_PER_SU["fp32_acc" if args.precision == "mixed" else "fp32"]
+        a32 = b32 * sites_per_launch / (stats[0][1] / stats[0][0] / 1e3) / 1e9
         roof32 = {"bound": "hbm", "achieved": a32, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                   "frac": a32 / peaks["hbm_gbs"], "traffic": ncu_traffic("sweep_fp32"),
                   "avg_launch_ms": stats[0][1] / stats[0][0]}
@@ -392,17 +397,29 @@ def run_ours(args, rank, world, local_rank):
 
 
 def run_kernel_target(args):
-    """A short, fixed sequence of sweep launches on the workload's lattice,
-    for ncu captures: 3 sweeps of the chosen storage precision."""
+    """Short, fixed launch sequences on the workload's lattice for ncu captures.
+    fp32 / fp64 / mixed: 3 sweeps in that precision (mixed: FP32 sweeps that
+    accumulate g).  window: a bounded slice of one bench step -- 100 mixed
+    FP32 sweeps with theta checks every 20 and a master sync at 100, the switch
+    to the FP64 master, and 60 FP64 sweeps with checks."""
     from paper_1212_5221_gb300 import build, gf, inputs
 
     build.build_all()
-    dims = WORKLOAD["dims"]
-    U = inputs.links(dims, "smooth", WORKLOAD["eps"], WORKLOAD["field_seed"])
-    h = gf.gf_create(dims, WORKLOAD["gauge"], args.kernel_target)
+    W = WORKLOAD
+    dims = W["dims"]
+    U = inputs.links(dims, "smooth", W["eps"], W["field_seed"])
+    prec = "mixed" if args.kernel_target == "window" else args.kernel_target
+    h = gf.gf_create(dims, W["gauge"], prec)
     gf.gf_load_links(h, 0, U)
     gf.gf_random_gauge_transform(h, 1000)
-    gf.gf_sweep(h, "or", WORKLOAD["omega"], 3, observables=False)
+    if args.kernel_target == "window":
+        kw = dict(algo="or", param=W["omega"], theta_target=W["theta"], check_interval=W["check"],
+                  reunit_interval=W["reunit"], switch_theta=W["switch_theta"], raise_on_notconv=False)
+        gf.gf_fix(h, max_sweeps=100, **kw)
+        gf.gf_promote(h)
+        gf.gf_fix(h, max_sweeps=60, **kw)
+    else:
+        gf.gf_sweep(h, "or", W["omega"], 3, observables=False)
     F, T = gf.gf_functional_theta(h)
     gf.gf_destroy(h)
     print(json.dumps({"kernel_target": args.kernel_target, "F": float(F[0]), "theta": float(T[0])}))
@@ -422,8 +439,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-fp64-baseline", dest="fp64_baseline", action="store_false")
-    ap.add_argument("--kernel-target", choices=["fp32", "fp64"], default=None,
-                    help="only run 3 sweeps of the workload in this storage precision (for ncu)")
+    ap.add_argument("--kernel-target", choices=["fp32", "fp64", "mixed", "window"], default=None,
+                    help="only run a short, fixed launch sequence of the workload (for ncu)")
     args = ap.parse_args()
     if args.kernel_target:
         run_kernel_target(args)
