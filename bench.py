@@ -71,18 +71,18 @@ def kernel_source_hash():
 
 
 def ncu_traffic(kind):
-    """Per-launch DRAM bytes of the sweep kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    """Per-launch DRAM bytes of a sweep kernel from the committed ncu summary
+    (profiles/ncu_traffic.txt), if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     try:
         with open(path) as f:
-            d = json.load(f)
-    except (OSError, ValueError):
-        return None
-    e = d.get(kind)
-    if not e or e.get("source_hash") != kernel_source_hash():
-        return None
-    return e.get("dram_bytes_per_launch_full_size")
+            for line in f:
+                p = line.split()
+                if len(p) == 3 and not line.startswith("#") and p[0] == kind:
+                    return int(p[2]) if p[1] == kernel_source_hash() else None
+    except OSError:
+        pass
+    return None
 
 
 class Clocks:
@@ -279,7 +279,7 @@ def run_ours(args, rank, world, local_rank):
         b32 = BYTES_PER_SU["fp32_acc" if args.precision == "mixed" else "fp32"]
         roof = {"bound": "hbm", "achieved": b32 * sites_per_launch / avg_s / 1e9,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s"}
-        roof["traffic"] = ncu_traffic("sweep_fp32")
+        roof["traffic"] = ncu_traffic("sweep_fp32_acc" if args.precision == "mixed" else "sweep_fp32")
     elif dom == 1:
         roof = {"bound": "alu", "achieved": FLOP_PER_SU * sites_per_launch / avg_s / 1e12,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
@@ -307,7 +307,8 @@ def run_ours(args, rank, world, local_rank):
         b32 = BYTES_PER_SU["fp32_acc" if args.precision == "mixed" else "fp32"]
         a32 = b32 * sites_per_launch / (stats[0][1] / stats[0][0] / 1e3) / 1e9
         roof32 = {"bound": "hbm", "achieved": a32, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                  "frac": a32 / peaks["hbm_gbs"], "traffic": ncu_traffic("sweep_fp32"),
+                  "frac": a32 / peaks["hbm_gbs"],
+                  "traffic": ncu_traffic("sweep_fp32_acc" if args.precision == "mixed" else "sweep_fp32"),
                   "avg_launch_ms": stats[0][1] / stats[0][0]}
 
     out = {}
