@@ -168,6 +168,21 @@ print(json.dumps(dict(sweeps=n, seconds=dt)))
                       f"(after 1 warm-up sweep), {d['seconds']:.1f} s, single thread"}
 
 
+def reduce_over_ranks(elapsed, site_updates, device=None):
+    """Whole-job numbers for the replicas: the slowest rank's elapsed time and
+    the sum of the site-updates of all ranks.  Without an initialised process
+    group, the local values."""
+    import torch
+
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return float(elapsed), float(site_updates)
+    t_max = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    s_sum = torch.tensor([float(site_updates)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.all_reduce(s_sum, op=torch.distributed.ReduceOp.SUM)
+    return float(t_max.item()), float(s_sum.item())
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle on this workload, rank 0 only."""
     if rank != 0:
@@ -258,15 +273,7 @@ def run_ours(args, rank, world, local_rank):
     su = sum(r["site_updates"] for r in results)
     sweeps32 = sum(r["sweeps_fp32"] for r in results)
     sweeps64 = sum(r["sweeps_fp64"] for r in results)
-    if dist:
-        t = torch.tensor([elapsed, float(su)], device=dev, dtype=torch.float64)
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        tsum = t.clone()
-        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
-        elapsed_all, su_all = float(tmax[0]), float(tsum[1])
-    else:
-        elapsed_all, su_all = elapsed, float(su)
+    elapsed_all, su_all = reduce_over_ranks(elapsed, float(su), dev if dist else None)
 
     # roofline of the dominant kernel (largest total device time)
     peaks, peak_src = measured_peaks()

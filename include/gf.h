@@ -115,6 +115,10 @@ int gf_load_links_device(gf_ctx* ctx, int copy, const double* device_src);
  * U_0(x) <- g(x) U_0(x) g(x+0)^dag (Sec. 5.1). */
 int gf_store_links(gf_ctx* ctx, int copy, double* host);
 
+/* As gf_store_links for the time-slices [t0, t0+nt) only (host holds
+ * nt*Nx*Ny*Nz*4*18 doubles). */
+int gf_store_links_slab(gf_ctx* ctx, int copy, int t0, int nt, double* host);
+
 /* As gf_store_links, to device memory. */
 int gf_store_links_device(gf_ctx* ctx, int copy, double* device_dst);
 

@@ -70,6 +70,7 @@ def _load():
                             _U32, _V]),
         "or_anneal": (None, [_PI, _V, ctypes.c_int, _D, _D, ctypes.c_int, _U32, _U64, _U32]),
         "or_step_quaternion": (None, [_PD, ctypes.c_int, _D, _PD]),
+        "or_haar_field": (None, [_U64, _U32, ctypes.c_long, _U32, _V]),
         "or_mag_maximiser": (None, [_PD, _PD]),
     }
     for name, (res, args) in sig.items():
@@ -119,6 +120,13 @@ def gauge_transform(U, g):
 def haar_su3(seed, site, copy=0):
     out = np.empty((3, 3), np.complex128)
     _load().or_haar_su3(seed & (2**64 - 1), site, copy, out.ctypes.data)
+    return out
+
+
+def haar_field(seed, site0, n, copy=0):
+    """Haar g(x) of the random gauge transformation for sites site0 .. site0+n-1."""
+    out = np.empty((n, 3, 3), np.complex128)
+    _load().or_haar_field(seed & (2**64 - 1), site0, n, copy, out.ctypes.data)
     return out
 
 

@@ -763,3 +763,10 @@ void or_step_quaternion(const double m[4], int algo, double param, double g[4]) 
 
 /* The MAG maximiser for a Pauli vector x, exposed for the pins. */
 void or_mag_maximiser(const double x[3], double m[4]) { mag_maximiser(x, m); }
+
+/* g(x) = or_haar_su3(seed, site, copy) for the n sites site0 .. site0+n-1,
+ * written as n consecutive 3x3 matrices (for building the transformation of
+ * a sub-lattice cut out of a larger one). */
+void or_haar_field(uint64_t seed, uint32_t site0, long n, uint32_t copy, double* out) {
+  for (long k = 0; k < n; ++k) or_haar_su3(seed, site0 + (uint32_t)k, copy, out + 18 * k);
+}

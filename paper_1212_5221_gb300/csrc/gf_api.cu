@@ -44,7 +44,7 @@ constexpr size_t STAGING_BYTES = (size_t)256 << 20;
 size_t round_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t links32 = 0, links64 = 0, active = 0, partial = 0, obs = 0, staging = 0, total = 0;
+  size_t links32 = 0, links64 = 0, gscratch = 0, active = 0, partial = 0, obs = 0, staging = 0, total = 0;
   int slab_nt = 1;
 };
 
@@ -90,13 +90,15 @@ Layout make_layout(const int dims[4], int ncopies, int gauge, int prec) {
   const int NS64 = gauge == GF_COULOMB ? 5 : 4;
   if (prec != GF_FP64) L.links32 = round_up((size_t)ncopies * 2 * NS32 * G.Vh * 3 * sizeof(float4));
   if (prec != GF_FP32) L.links64 = round_up((size_t)ncopies * 2 * NS64 * G.Vh * 6 * sizeof(double2));
+  // GF_MIXED: the re-unitarised FP64 accumulator, full 3x3, used by the master sync
+  if (prec == GF_MIXED) L.gscratch = round_up((size_t)ncopies * 2 * G.Vh * 9 * sizeof(double2));
   L.active = round_up((size_t)ncopies * dims[0] * sizeof(int));
   L.partial = round_up(gfk::observables_partial_doubles(G, ncopies) * sizeof(double));
   L.obs = round_up((size_t)ncopies * dims[0] * 2 * sizeof(double));
   const size_t slice_bytes = (size_t)G.V3 * 4 * 18 * sizeof(double);
   L.slab_nt = (int)std::max<size_t>(1, std::min<size_t>(dims[0], STAGING_BYTES / slice_bytes));
   L.staging = round_up((size_t)L.slab_nt * slice_bytes);
-  L.total = L.links32 + L.links64 + L.active + L.partial + L.obs + L.staging;
+  L.total = L.links32 + L.links64 + L.gscratch + L.active + L.partial + L.obs + L.staging;
   return L;
 }
 
@@ -115,6 +117,7 @@ struct gf_ctx {
   void* owned = nullptr;  // device block allocated by the context (nullptr for gf_create_ext)
   void* links32 = nullptr;
   void* links64 = nullptr;
+  void* gscratch = nullptr;
   int* active_d = nullptr;
   double* partial = nullptr;
   double* obs_d = nullptr;
@@ -325,10 +328,11 @@ int set_identity_slots(gf_ctx* c, int first, int last) {
 int sync_master(gf_ctx* c) {
   if (c->prec != GF_MIXED || c->fp64 || !c->dirty) return GF_OK;
   cudaEvent_t t0 = prof_begin(c);
-  cudaError_t e = gfk::launch_sync_master(c->links32, c->links64, c->G, c->NS32, c->NS64, c->ncopies, c->st);
+  cudaError_t e =
+      gfk::launch_sync_master(c->links32, c->links64, c->gscratch, c->G, c->NS32, c->NS64, c->ncopies, c->st);
   if (e != cudaSuccess) return fail(GF_ECUDA, "sync: %s", cudaGetErrorString(e));
   prof_end(c, t0, GF_KERNEL_OTHER);
-  c->launch_count += 2;
+  c->launch_count += 3;
   c->dirty = false;
   return GF_OK;
 }
@@ -409,6 +413,7 @@ int create_impl(const int dims[4], int ncopies, int gauge, int prec, void* strea
   size_t off = 0;
   if (L.links32) { c->links32 = base + off; off += L.links32; }
   if (L.links64) { c->links64 = base + off; off += L.links64; }
+  if (L.gscratch) { c->gscratch = base + off; off += L.gscratch; }
   c->active_d = reinterpret_cast<int*>(base + off); off += L.active;
   c->partial = reinterpret_cast<double*>(base + off); off += L.partial;
   c->obs_d = reinterpret_cast<double*>(base + off); off += L.obs;
@@ -645,6 +650,24 @@ int gf_store_links(gf_ctx* c, int copy, double* host) {
   return GF_OK;
 }
 
+int gf_store_links_slab(gf_ctx* c, int copy, int t0, int nt, double* host) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if ((r = check_copy(c, copy, false))) return r;
+  if (!host) return fail(GF_EINVAL, "host is NULL");
+  if (t0 < 0 || nt < 1 || t0 + nt > c->dims[0]) return fail(GF_EINVAL, "slab [%d,%d) outside [0,%d)", t0, t0 + nt, c->dims[0]);
+  if ((r = consolidate(c))) return r;
+  const size_t per_t = (size_t)c->G.V3 * 4 * 18;
+  for (int t = t0; t < t0 + nt; t += c->layout.slab_nt) {
+    const int n = std::min(c->layout.slab_nt, t0 + nt - t);
+    if ((r = export_slab(c, copy, t, n, c->staging))) return r;
+    GF_CUDA(cudaMemcpyAsync(host + (size_t)(t - t0) * per_t, c->staging, (size_t)n * per_t * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->st));
+  }
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  return GF_OK;
+}
+
 int gf_store_links_device(gf_ctx* c, int copy, double* dev) {
   int r = check_ctx(c);
   if (r) return r;
@@ -862,7 +885,11 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
   std::vector<double> ct;
   std::vector<double> unit_theta((size_t)c->ncopies * units_per_copy);
   double best_fp32 = INFINITY;
-  int stall = 0;
+  int best_at = 0;  // sweep count when the FP32 stage last improved theta
+  // adaptive checks: theta falls geometrically in the tail, so after two
+  // checks the next one is scheduled near the predicted crossing
+  double prev_worst = -1.0;
+  int prev_sweeps = 0;
   int since_reunit = 0;
   for (;;) {
     if ((r = observables(c, ct))) return r;
@@ -906,16 +933,25 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
       // (its rounding floor) for 25 consecutive checks
       if (worst < best_fp32) {
         best_fp32 = worst;
-        stall = 0;
-      } else {
-        stall++;
+        best_at = R.sweeps;
       }
-      if (worst < P->switch_theta || stall >= 25 || !std::isfinite(worst)) {
+      const bool stalled = R.sweeps - best_at >= 25 * P->check_interval;
+      if (worst < P->switch_theta || stalled || !std::isfinite(worst)) {
         if ((r = promote(c))) return r;
+        prev_worst = -1.0;
         continue;  // re-evaluate theta in FP64
       }
     }
-    const int k = std::min(P->check_interval, P->max_sweeps - R.sweeps);
+    const double thr = (!c->fp64 && c->prec == GF_MIXED) ? P->switch_theta : P->theta_target;
+    int k = P->check_interval;
+    if (prev_worst > 0 && worst < prev_worst && worst > thr && R.sweeps > prev_sweeps) {
+      const double rate = std::log(prev_worst / worst) / (double)(R.sweeps - prev_sweeps);
+      const double need = std::log(worst / thr) / rate;
+      k = (int)std::min<double>(10.0 * P->check_interval, std::max<double>(P->check_interval, 0.7 * need));
+    }
+    prev_worst = worst;
+    prev_sweeps = R.sweeps;
+    k = std::min(k, P->max_sweeps - R.sweeps);
     for (int i = 0; i < k; ++i) {
       if ((r = api_sweep(c, P->algo, P->param, P->seed))) return r;
       R.site_updates += (uint64_t)n_active * sites_per_unit;

@@ -65,7 +65,7 @@ cudaError_t launch_export(double* nat, const void* links, const Geom& G, int NS,
 template <typename R>
 cudaError_t launch_haar_transform(void* links, const Geom& G, int NS, uint32_t ncopies, uint32_t copy0,
                                   uint64_t seed, cudaStream_t st) {
-  const uint64_t n = (uint64_t)ncopies * G.Vh * 8;
+  const uint64_t n = (uint64_t)ncopies * G.Vh;
   for (int p = 0; p < 2; ++p) {
     haar_transform_kernel<R><<<nblocks(n), BLOCK, 0, st>>>(static_cast<typename store_traits<R>::vec*>(links),
                                                             G, NS, p, ncopies, copy0, (uint32_t)seed,
@@ -101,12 +101,18 @@ cudaError_t launch_philox(const void* ctr, void* out, uint64_t n, uint64_t seed,
   return cudaGetLastError();
 }
 
-cudaError_t launch_sync_master(void* l32, void* l64, const Geom& G, int NS32, int NS64, uint32_t ncopies,
-                               cudaStream_t st) {
-  const uint64_t n = (uint64_t)ncopies * G.V * 4;
-  sync_master_kernel<<<nblocks(n), BLOCK, 0, st>>>(static_cast<float4*>(l32), static_cast<double2*>(l64), G,
-                                                    NS32, NS64, ncopies);
+cudaError_t launch_sync_master(void* l32, void* l64, void* gscratch, const Geom& G, int NS32, int NS64,
+                               uint32_t ncopies, cudaStream_t st) {
+  const uint64_t nsites = (uint64_t)ncopies * 2 * G.Vh;
+  prepare_g_kernel<<<nblocks(nsites), BLOCK, 0, st>>>(static_cast<const float4*>(l32),
+                                                       static_cast<double2*>(gscratch), G.Vh, NS32, nsites);
   cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const uint64_t n = (uint64_t)ncopies * G.V * 4;
+  sync_master_kernel<<<nblocks(n), BLOCK, 0, st>>>(static_cast<const double2*>(gscratch),
+                                                    static_cast<float4*>(l32), static_cast<double2*>(l64), G,
+                                                    NS32, NS64, ncopies);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_identity_slot<float>(l32, G, NS32, 4, ncopies, st);
 }

@@ -238,16 +238,14 @@ __global__ void __launch_bounds__(BLOCK) export_kernel(double* __restrict__ nat,
 // g(x), done as two passes over the sublattices: sites of one parity apply
 // their g(x) from the left to U_mu(x) and from the right (as g^dag) to
 // U_mu(x-mu).  Every link has one endpoint of each parity, so after both
-// passes it carries g(x) ... g(x+mu)^dag.  Eight lanes per site, one link
-// each; every lane regenerates g(x) from the counter-based generator.
+// passes it carries g(x) ... g(x+mu)^dag.  One thread per site draws g(x)
+// once from the counter-based generator and updates the site's eight links.
 template <typename R>
 __global__ void __launch_bounds__(BLOCK) haar_transform_kernel(typename store_traits<R>::vec* links, Geom G,
                                                                int NS, int parity, uint32_t ncopies,
                                                                uint32_t copy0, uint32_t k0, uint32_t k1) {
   constexpr int NC = store_traits<R>::NC;
-  const uint64_t tid = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
-  const uint64_t gsite = tid >> 3;
-  const int k = (int)(tid & 7);
+  const uint64_t gsite = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
   const uint32_t copy = (uint32_t)(gsite / G.Vh);
   if (copy >= ncopies) return;
   const uint32_t sp = (uint32_t)(gsite - (uint64_t)copy * G.Vh);
@@ -257,36 +255,39 @@ __global__ void __launch_bounds__(BLOCK) haar_transform_kernel(typename store_tr
   Rng rng{k0, k1, s, 0u, copy0 + copy};
   mat3<R> g;
   haar_su3(rng, g);
-  const int mu = k & 3;
-  const bool down = k >= 4;
-  size_t off = down ? link_off(copy, parity ^ 1, mu, NS, NC, G.Vh, site_minus(G, s, c, mu) >> 1)
-                    : link_off(copy, parity, mu, NS, NC, G.Vh, sp);
-  mat3<R> u, r;
-  load_rows(links + off, G.Vh, u);
-  reconstruct_row2(u);
+#pragma unroll 1
+  for (int k = 0; k < 8; ++k) {
+    const int mu = k >> 1;
+    const bool down = k & 1;
+    const size_t off = down ? link_off(copy, parity ^ 1, mu, NS, NC, G.Vh, site_minus(G, s, c, mu) >> 1)
+                            : link_off(copy, parity, mu, NS, NC, G.Vh, sp);
+    mat3<R> u, r;
+    load_rows(links + off, G.Vh, u);
+    reconstruct_row2(u);
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      cx<R> acc{R(0), R(0)};
-      if (!down) {  // (g u)_ab
+      for (int b = 0; b < 3; ++b) {
+        cx<R> acc{R(0), R(0)};
+        if (!down) {  // (g u)_ab
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          cx<R> t = cmul(g.e[a][q], u.e[q][b]);
-          acc.re += t.re;
-          acc.im += t.im;
+          for (int q = 0; q < 3; ++q) {
+            cx<R> t = cmul(g.e[a][q], u.e[q][b]);
+            acc.re += t.re;
+            acc.im += t.im;
+          }
+        } else {  // (u g^dag)_ab = sum_q u_aq conj(g_bq)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            cx<R> t = cmul(u.e[a][q], cx<R>{g.e[b][q].re, -g.e[b][q].im});
+            acc.re += t.re;
+            acc.im += t.im;
+          }
         }
-      } else {  // (u g^dag)_ab = sum_q u_aq conj(g_bq)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          cx<R> t = cmul(u.e[a][q], cx<R>{g.e[b][q].re, -g.e[b][q].im});
-          acc.re += t.re;
-          acc.im += t.im;
-        }
+        r.e[a][b] = acc;
       }
-      r.e[a][b] = acc;
-    }
-  store_rows(links + off, G.Vh, r);
+    store_rows(links + off, G.Vh, r);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -375,22 +376,41 @@ __global__ void philox_kernel(const uint4* ctr, uint4* out, uint64_t n, uint32_t
 // the FP32 sweeps (slot 4 of the FP32 array) to the FP64 links,
 // U_mu(x) <- G(x) U_mu(x) G(x+mu)^dag in FP64 with G re-unitarised in FP64,
 // and write the result back to both arrays (the FP32 copy re-rounded from the
-// exact one).  One thread per (site, mu).  The accumulator is reset by a
-// separate launch once every thread has read it.
-__device__ __forceinline__ void load_g_fp64(const float4* l32, uint32_t copy, int p, int NS32, uint32_t Vh,
-                                            uint32_t sp, mat3<double>& g) {
+// exact one).  First pass: one thread per site re-unitarises G(x) in FP64
+// and keeps the full 3x3 in a scratch array ([copy][parity][9][Vh] double2).
+// Second pass: one thread per (site, mu) forms rows 0 and 1 of
+// G(x) U G(x+mu)^dag.  The accumulator is reset by a third launch.
+__global__ void __launch_bounds__(BLOCK) prepare_g_kernel(const float4* l32, double2* gs, uint32_t Vh, int NS32,
+                                                          uint64_t nsites) {
+  const uint64_t m = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (m >= nsites) return;
+  const uint64_t cp = m / Vh, sp = m - cp * Vh;  // cp = copy*2 + parity
   mat3<float> f;
-  load_rows(l32 + link_off(copy, p, 4, NS32, 3, Vh, sp), Vh, f);
+  load_rows(l32 + ((cp * NS32 + 4) * 3) * Vh + sp, Vh, f);
+  mat3<double> g;
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) g.e[a][b] = {(double)f.e[a][b].re, (double)f.e[a][b].im};
   gram_schmidt_rows(g);
   reconstruct_row2(g);
+  double2* o = gs + cp * 9 * Vh + sp;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) o[(size_t)k * Vh] = make_double2(g.e[k / 3][k % 3].re, g.e[k / 3][k % 3].im);
 }
 
-__global__ void __launch_bounds__(BLOCK) sync_master_kernel(float4* l32, double2* l64, Geom G, int NS32, int NS64,
-                                                            uint32_t ncopies) {
+__device__ __forceinline__ void load_g9(const double2* gs, uint32_t copy, int p, uint32_t Vh, uint32_t sp,
+                                        mat3<double>& g) {
+  const double2* q = gs + ((size_t)copy * 2 + p) * 9 * Vh + sp;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    double2 v = q[(size_t)k * Vh];
+    g.e[k / 3][k % 3] = {v.x, v.y};
+  }
+}
+
+__global__ void __launch_bounds__(BLOCK) sync_master_kernel(const double2* gs, float4* l32, double2* l64, Geom G,
+                                                            int NS32, int NS64, uint32_t ncopies) {
   const uint64_t tid = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
   const uint64_t per_copy = (uint64_t)G.V * 4;
   const uint32_t copy = (uint32_t)(tid / per_copy);
@@ -403,14 +423,16 @@ __global__ void __launch_bounds__(BLOCK) sync_master_kernel(float4* l32, double2
   int c[4];
   uint32_t s;
   site_coords(G, sp, p, c, s);
-  mat3<double> gx, gy, u, t;
-  load_g_fp64(l32, copy, p, NS32, G.Vh, sp, gx);
-  load_g_fp64(l32, copy, p ^ 1, NS32, G.Vh, site_plus(G, s, c, mu) >> 1, gy);
+  mat3<double> gx, gy, u;
+  load_g9(gs, copy, p, G.Vh, sp, gx);
+  load_g9(gs, copy, p ^ 1, G.Vh, site_plus(G, s, c, mu) >> 1, gy);
   const size_t off64 = link_off(copy, p, mu, NS64, 6, G.Vh, sp);
   load_rows(l64 + off64, G.Vh, u);
   reconstruct_row2(u);
+  // rows 0, 1 of G(x) U, then times G(x+mu)^dag
+  cx<double> t[2][3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       cx<double> acc{0.0, 0.0};
@@ -420,7 +442,7 @@ __global__ void __launch_bounds__(BLOCK) sync_master_kernel(float4* l32, double2
         acc.re += v.re;
         acc.im += v.im;
       }
-      t.e[a][b] = acc;
+      t[a][b] = acc;
     }
   mat3<float> f;
 #pragma unroll
@@ -430,7 +452,7 @@ __global__ void __launch_bounds__(BLOCK) sync_master_kernel(float4* l32, double2
       cx<double> acc{0.0, 0.0};
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        cx<double> v = cmul(t.e[a][q], cx<double>{gy.e[b][q].re, -gy.e[b][q].im});
+        cx<double> v = cmul(t[a][q], cx<double>{gy.e[b][q].re, -gy.e[b][q].im});
         acc.re += v.re;
         acc.im += v.im;
       }

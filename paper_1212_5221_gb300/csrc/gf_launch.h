@@ -43,8 +43,8 @@ cudaError_t launch_identity_slot(void* links, const Geom& G, int NS, int slot, u
 // Mixed precision with an FP64 master: apply the FP32-accumulated gauge
 // transformation (slot 4) to the FP64 links and re-round the FP32 copy, then
 // reset the accumulator; and the plain FP64 -> FP32 copy (accumulator = 1).
-cudaError_t launch_sync_master(void* l32, void* l64, const Geom& G, int NS32, int NS64, uint32_t ncopies,
-                               cudaStream_t st);
+cudaError_t launch_sync_master(void* l32, void* l64, void* gscratch, const Geom& G, int NS32, int NS64,
+                               uint32_t ncopies, cudaStream_t st);
 cudaError_t launch_demote(const void* l64, void* l32, const Geom& G, int NS64, int NS32, uint32_t ncopies,
                           cudaStream_t st);
 

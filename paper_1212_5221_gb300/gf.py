@@ -68,6 +68,7 @@ _SIG = {
     "gf_load_links_device": [_P, _I, _P],
     "gf_store_links": [_P, _I, _P],
     "gf_store_links_device": [_P, _I, _P],
+    "gf_store_links_slab": [_P, _I, _I, _I, _P],
     "gf_random_gauge_transform": [_P, ctypes.c_uint64],
     "gf_sweep": [_P, _I, _D, _I, ctypes.c_uint64, _P, _P],
     "gf_anneal": [_P, _D, _D, _I, ctypes.c_uint64, _P, _P],
@@ -193,6 +194,10 @@ def gf_load_links_device(h, copy, dev_ptr: int):
 
 def gf_store_links(h, copy, out):
     _check(lib().gf_store_links(h, copy, _links_arg(out)), "gf_store_links")
+
+
+def gf_store_links_slab(h, copy, t0, nt, out):
+    _check(lib().gf_store_links_slab(h, copy, t0, nt, _links_arg(out)), "gf_store_links_slab")
 
 
 def gf_store_links_device(h, copy, dev_ptr: int):
