@@ -184,6 +184,16 @@ int gf_set_links_per_thread(gf_ctx* ctx, int lpt);
  * bulk prefetches while the current tile is processed.  Results do not
  * depend on this switch. */
 int gf_set_prefetch(gf_ctx* ctx, int on);
+
+/* F and theta fused into the sweeps (on by default): the odd half of the last
+ * overrelaxation/relaxation sweep -- in which every link is written exactly
+ * once -- also sums F over the links it writes and theta of its sites from
+ * K(x) = sum of the updated links, in FP64; a read-only pass of the sweep
+ * kernel gathers K at the even sites; the per-site values are added per
+ * (copy, time-slice) in a fixed order.  Used by gf_fix's checks and by
+ * gf_sweep(GF_OR / GF_RELAX) when F or theta is requested.  Off: the
+ * standalone observables pass (same values up to summation order). */
+int gf_set_fused_observables(gf_ctx* ctx, int on);
 int gf_get_links_per_thread(gf_ctx* ctx, int* lpt);
 int gf_autotune(gf_ctx* ctx, gf_algo algo, int* best_lpt, double* ms_per_sweep_best);
 

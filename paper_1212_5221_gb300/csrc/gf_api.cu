@@ -44,7 +44,8 @@ constexpr size_t STAGING_BYTES = (size_t)256 << 20;
 size_t round_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t links32 = 0, links64 = 0, gscratch = 0, active = 0, partial = 0, obs = 0, staging = 0, total = 0;
+  size_t links32 = 0, links64 = 0, gscratch = 0, obs_site = 0, active = 0, partial = 0, obs = 0, staging = 0,
+         total = 0;
   int slab_nt = 1;
 };
 
@@ -92,13 +93,14 @@ Layout make_layout(const int dims[4], int ncopies, int gauge, int prec) {
   if (prec != GF_FP32) L.links64 = round_up((size_t)ncopies * 2 * NS64 * G.Vh * 6 * sizeof(double2));
   // GF_MIXED: the re-unitarised FP64 accumulator, full 3x3, used by the master sync
   if (prec == GF_MIXED) L.gscratch = round_up((size_t)ncopies * 2 * G.Vh * 9 * sizeof(double2));
+  L.obs_site = round_up((size_t)ncopies * G.V * sizeof(double2));  // fused per-site F/theta
   L.active = round_up((size_t)ncopies * dims[0] * sizeof(int));
   L.partial = round_up(gfk::observables_partial_doubles(G, ncopies) * sizeof(double));
   L.obs = round_up((size_t)ncopies * dims[0] * 2 * sizeof(double));
   const size_t slice_bytes = (size_t)G.V3 * 4 * 18 * sizeof(double);
   L.slab_nt = (int)std::max<size_t>(1, std::min<size_t>(dims[0], STAGING_BYTES / slice_bytes));
   L.staging = round_up((size_t)L.slab_nt * slice_bytes);
-  L.total = L.links32 + L.links64 + L.gscratch + L.active + L.partial + L.obs + L.staging;
+  L.total = L.links32 + L.links64 + L.gscratch + L.obs_site + L.active + L.partial + L.obs + L.staging;
   return L;
 }
 
@@ -118,6 +120,7 @@ struct gf_ctx {
   void* links32 = nullptr;
   void* links64 = nullptr;
   void* gscratch = nullptr;
+  void* obs_site = nullptr;
   int* active_d = nullptr;
   double* partial = nullptr;
   double* obs_d = nullptr;
@@ -129,6 +132,7 @@ struct gf_ctx {
   uint64_t sweep_index = 0;
   uint32_t copy_base = 0;  // Philox copy id of copy 0
   int prefetch = 1;        // L2 prefetch of the next tile in the sweep kernels
+  int fused_obs = 1;       // F/theta fused into the last OR sweep where possible
   int lpt[2][5] = {{0}};  // [fp64][algo] chosen links per thread, 0 = default
   // optional per-kernel timing: CUDA events around every launch of a class
   uint64_t launch_count = 0;  // every kernel this context launched
@@ -199,7 +203,8 @@ int default_lpt(const gf_ctx* c, int algo) {
   return c->fp64 ? 8 : 4;  // fastest on GB300 for the 32^3 x 64 Landau sweep
 }
 
-int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, uint32_t sweep, int lpt) {
+int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, uint32_t sweep, int lpt,
+                int obs = 0, int update = 1) {
   cudaError_t e;
   if (c->fp64) {
     gfk::SweepArgs<double> a;
@@ -215,7 +220,10 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     a.k1 = (uint32_t)(seed >> 32);
     a.sweep = sweep;
     a.prefetch = c->prefetch;
-    a.acc = (c->prec == GF_MIXED && !c->fp64 && c->gauge != GF_COULOMB) ? 1 : 0;
+    a.acc = (update && c->prec == GF_MIXED && !c->fp64 && c->gauge != GF_COULOMB) ? 1 : 0;
+    a.obs = obs;
+    a.update = update;
+    a.obs_site = static_cast<double2*>(c->obs_site);
     cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<double>(a, c->gauge, kalgo, lpt, c->st);
     prof_end(c, t0, GF_KERNEL_SWEEP_FP64);
@@ -234,7 +242,10 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     a.k1 = (uint32_t)(seed >> 32);
     a.sweep = sweep;
     a.prefetch = c->prefetch;
-    a.acc = (c->prec == GF_MIXED && !c->fp64 && c->gauge != GF_COULOMB) ? 1 : 0;
+    a.acc = (update && c->prec == GF_MIXED && !c->fp64 && c->gauge != GF_COULOMB) ? 1 : 0;
+    a.obs = obs;
+    a.update = update;
+    a.obs_site = static_cast<double2*>(c->obs_site);
     cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<float>(a, c->gauge, kalgo, lpt, c->st);
     prof_end(c, t0, GF_KERNEL_SWEEP_FP32);
@@ -244,12 +255,14 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
   return GF_OK;
 }
 
-// One full sweep (even, then odd sublattice) of kernel algorithm kalgo.
-int full_sweep(gf_ctx* c, int kalgo, int api_algo, double param, uint64_t seed, int lpt_override = 0) {
+// One full sweep (even, then odd sublattice) of kernel algorithm kalgo; with
+// obs_last the odd half also writes F and theta of its sites (fused check).
+int full_sweep(gf_ctx* c, int kalgo, int api_algo, double param, uint64_t seed, int lpt_override = 0,
+               bool obs_last = false) {
   const int lpt = lpt_override ? lpt_override : default_lpt(c, api_algo);
   const uint32_t sw = (uint32_t)c->sweep_index;
   for (int p = 0; p < 2; ++p) {
-    int r = launch_half(c, kalgo, param, p, seed, sw, lpt);
+    int r = launch_half(c, kalgo, param, p, seed, sw, lpt, (obs_last && p == 1) ? 2 : 0);
     if (r) return r;
   }
   if (c->prec == GF_MIXED && !c->fp64) c->dirty = true;
@@ -276,6 +289,25 @@ int observables_on(gf_ctx* c, std::vector<double>& per_ct, bool f64) {
 
 // observables of the storage the sweeps run on
 int observables(gf_ctx* c, std::vector<double>& per_ct) { return observables_on(c, per_ct, c->fp64); }
+
+// Observables from the fused sweeps: the odd half of the last sweep wrote F
+// and theta of the odd sites; a read-only pass of the sweep kernel gathers K
+// at the even sites; both are summed per (copy, slice).
+int fused_observables(gf_ctx* c, std::vector<double>& per_ct) {
+  cudaEvent_t t0 = prof_begin(c);
+  int r = launch_half(c, gfk::ALG_OR, 1.0, 0, 0, 0, default_lpt(c, GF_OR), 1, 0);
+  if (r) return r;
+  cudaError_t e = gfk::launch_obs_site_reduce(c->obs_site, c->G, c->gauge, c->ncopies, c->partial, c->obs_d, c->st);
+  if (e != cudaSuccess) return fail(GF_ECUDA, "fused observables: %s", cudaGetErrorString(e));
+  prof_end(c, t0, GF_KERNEL_OBSERVABLES);
+  c->launch_count += 2;
+  per_ct.resize((size_t)c->ncopies * c->dims[0] * 2);
+  GF_CUDA(cudaMemcpyAsync(per_ct.data(), c->obs_d, per_ct.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->st));
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  prof_collect(c);
+  return GF_OK;
+}
 
 void copy_means(const gf_ctx* c, const std::vector<double>& ct, double* F, double* T) {
   const int Nt = c->dims[0];
@@ -414,6 +446,7 @@ int create_impl(const int dims[4], int ncopies, int gauge, int prec, void* strea
   if (L.links32) { c->links32 = base + off; off += L.links32; }
   if (L.links64) { c->links64 = base + off; off += L.links64; }
   if (L.gscratch) { c->gscratch = base + off; off += L.gscratch; }
+  c->obs_site = base + off; off += L.obs_site;
   c->active_d = reinterpret_cast<int*>(base + off); off += L.active;
   c->partial = reinterpret_cast<double*>(base + off); off += L.partial;
   c->obs_d = reinterpret_cast<double*>(base + off); off += L.obs;
@@ -497,10 +530,10 @@ int check_algo_param(int algo, double param) {
 }
 
 // One API-level sweep: SA = heat bath + 3 microcanonical sweeps.
-int api_sweep(gf_ctx* c, int algo, double param, uint64_t seed) {
+int api_sweep(gf_ctx* c, int algo, double param, uint64_t seed, bool obs_last = false) {
   switch (algo) {
-    case GF_RELAX: return full_sweep(c, gfk::ALG_OR, GF_RELAX, 1.0, seed);
-    case GF_OR: return full_sweep(c, gfk::ALG_OR, GF_OR, param, seed);
+    case GF_RELAX: return full_sweep(c, gfk::ALG_OR, GF_RELAX, 1.0, seed, 0, obs_last);
+    case GF_OR: return full_sweep(c, gfk::ALG_OR, GF_OR, param, seed, 0, obs_last);
     case GF_MICRO: return full_sweep(c, gfk::ALG_MICRO, GF_MICRO, 0.0, seed);
     case GF_SR: return full_sweep(c, gfk::ALG_SR, GF_SR, param, seed);
     case GF_SA: {
@@ -698,8 +731,19 @@ int gf_sweep(gf_ctx* c, gf_algo algo, double param, int n_sweeps, uint64_t seed,
   if (r) return r;
   if ((r = check_algo_param(algo, param))) return r;
   if (n_sweeps < 0) return fail(GF_EINVAL, "n_sweeps < 0");
+  // fused observables: the odd half of the last sweep writes F/theta of its
+  // sites (only when those links are the final ones: not in the FP32 stage of
+  // GF_MIXED, whose master is read instead)
+  const bool fused = c->fused_obs && (F || theta) && n_sweeps > 0 && (algo == GF_OR || algo == GF_RELAX) &&
+                     !(c->prec == GF_MIXED && !c->fp64);
   for (int k = 0; k < n_sweeps; ++k)
-    if ((r = api_sweep(c, algo, param, seed))) return r;
+    if ((r = api_sweep(c, algo, param, seed, fused && k == n_sweeps - 1))) return r;
+  if (fused) {
+    std::vector<double> ct;
+    if ((r = fused_observables(c, ct))) return r;
+    copy_means(c, ct, F, theta);
+    return GF_OK;
+  }
   return finish_public(c, F, theta);
 }
 
@@ -791,6 +835,13 @@ int gf_set_copy_base(gf_ctx* c, uint32_t base) {
   int r = check_ctx(c);
   if (r) return r;
   c->copy_base = base;
+  return GF_OK;
+}
+
+int gf_set_fused_observables(gf_ctx* c, int on) {
+  int r = check_ctx(c);
+  if (r) return r;
+  c->fused_obs = on ? 1 : 0;
   return GF_OK;
 }
 
@@ -890,9 +941,13 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
   // checks the next one is scheduled near the predicted crossing
   double prev_worst = -1.0;
   int prev_sweeps = 0;
+  bool fused_ready = false;  // the last sweep's odd half wrote F/theta of its sites
   int since_reunit = 0;
   for (;;) {
-    if ((r = observables(c, ct))) return r;
+    // theta after the last sweep: fused into its odd half when nothing has
+    // touched the links since, else the standalone pass
+    if ((r = (fused_ready && c->fused_obs) ? fused_observables(c, ct) : observables(c, ct))) return r;
+    fused_ready = false;
     R.checks++;
     // theta per unit: a copy (Landau/MAG, mean over slices) or a time-slice (Coulomb)
     double worst = 0;
@@ -939,7 +994,7 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
       if (worst < P->switch_theta || stalled || !std::isfinite(worst)) {
         if ((r = promote(c))) return r;
         prev_worst = -1.0;
-        continue;  // re-evaluate theta in FP64
+        continue;  // re-evaluate theta in FP64 (standalone pass)
       }
     }
     const double thr = (!c->fp64 && c->prec == GF_MIXED) ? P->switch_theta : P->theta_target;
@@ -953,7 +1008,9 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
     prev_sweeps = R.sweeps;
     k = std::min(k, P->max_sweeps - R.sweeps);
     for (int i = 0; i < k; ++i) {
-      if ((r = api_sweep(c, P->algo, P->param, P->seed))) return r;
+      const bool last = i == k - 1;
+      if ((r = api_sweep(c, P->algo, P->param, P->seed, last))) return r;
+      if (last) fused_ready = true;
       R.site_updates += (uint64_t)n_active * sites_per_unit;
       if (c->fp64) {
         R.sweeps_fp64++;
@@ -962,6 +1019,7 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
         if (P->reunit_interval > 0 && ++since_reunit >= P->reunit_interval) {
           since_reunit = 0;
           if ((r = reunitarize(c))) return r;
+          fused_ready = false;  // the links changed after the fused half-sweep
         }
       }
     }

@@ -127,6 +127,19 @@ cudaError_t launch_demote(const void* l64, void* l32, const Geom& G, int NS64, i
   return launch_identity_slot<float>(l32, G, NS32, 4, ncopies, st);
 }
 
+cudaError_t launch_obs_site_reduce(const void* obs_site, const Geom& G, int gauge, uint32_t ncopies, double* partial,
+                                   double* out, cudaStream_t st) {
+  const uint32_t bps = (G.V3 / 2 + BLOCK - 1) / BLOCK;  // fits the observables partial buffer
+  const uint32_t nct = ncopies * (uint32_t)G.n[0];
+  obs_site_reduce<<<dim3(bps, nct), BLOCK, 0, st>>>(static_cast<const double2*>(obs_site), G.V3, bps, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nd = gauge == COULOMB ? 3 : 4;
+  obs_site_finish<<<(nct + 127) / 128, 128, 0, st>>>(partial, bps, nct, 1.0 / (3.0 * nd * (double)G.V3),
+                                                      1.0 / (3.0 * (double)G.V3), out);
+  return cudaGetLastError();
+}
+
 #define GF_INST(R)                                                                                         \
   template cudaError_t launch_observables<R>(const void*, const Geom&, int, int, uint32_t, double*, double*, \
                                              cudaStream_t);                                              \

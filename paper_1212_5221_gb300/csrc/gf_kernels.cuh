@@ -481,5 +481,54 @@ __global__ void __launch_bounds__(BLOCK) demote_kernel(const double2* l64, float
   store_rows(l32 + ((cp * NS32 + mu) * 3) * Vh + sp, Vh, f);
 }
 
+// ---------------------------------------------------------------------------
+// Reduction of the per-site observables the fused sweeps wrote
+// ([copy][site] double2 (F, theta)): per (copy, time-slice) unit, block
+// partials over the slice's contiguous sites, then a fixed-order sum.
+__global__ void __launch_bounds__(BLOCK) obs_site_reduce(const double2* obs_site, uint32_t V3, uint32_t bps,
+                                                         double* partial) {
+  const uint32_t ct = blockIdx.y;
+  const double2* q = obs_site + (size_t)ct * V3;
+  double f = 0, th = 0;
+  for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < V3; i += bps * BLOCK) {
+    const double2 v = q[i];
+    f += v.x;
+    th += v.y;
+  }
+  __shared__ double sf[BLOCK / 32], st[BLOCK / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    f += __shfl_xor_sync(FULL, f, o);
+    th += __shfl_xor_sync(FULL, th, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sf[threadIdx.x / 32] = f;
+    st[threadIdx.x / 32] = th;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double F = 0, T = 0;
+    for (int k = 0; k < BLOCK / 32; ++k) {
+      F += sf[k];
+      T += st[k];
+    }
+    partial[((size_t)ct * bps + blockIdx.x) * 2] = F;
+    partial[((size_t)ct * bps + blockIdx.x) * 2 + 1] = T;
+  }
+}
+
+__global__ void obs_site_finish(const double* partial, uint32_t bps, uint32_t nct, double normF, double normT,
+                                double* out) {
+  const uint32_t ct = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ct >= nct) return;
+  double F = 0, T = 0;
+  for (uint32_t b = 0; b < bps; ++b) {
+    F += partial[((size_t)ct * bps + b) * 2];
+    T += partial[((size_t)ct * bps + b) * 2 + 1];
+  }
+  out[2 * ct] = F * normF;
+  out[2 * ct + 1] = T * normT;
+}
+
 }  // namespace gfk
 

@@ -48,6 +48,10 @@ cudaError_t launch_sync_master(void* l32, void* l64, void* gscratch, const Geom&
 cudaError_t launch_demote(const void* l64, void* l32, const Geom& G, int NS64, int NS32, uint32_t ncopies,
                           cudaStream_t st);
 
+// Per-(copy, slice) F/theta from the per-site values the fused sweeps wrote.
+cudaError_t launch_obs_site_reduce(const void* obs_site, const Geom& G, int gauge, uint32_t ncopies, double* partial,
+                                   double* out, cudaStream_t st);
+
 // Record the calling thread's error message (read by gf_last_error).
 void set_last_error(const char* msg);
 

@@ -23,7 +23,97 @@ struct SweepArgs {
   int prefetch;       // 1: prefetch the next tile into L2
   int acc;            // 1: slot 4 accumulates g(x) (mixed precision; never for Coulomb,
                       //    whose slot 0 already does)
+  int obs;            // fused observables: 0 none; 1 theta of the gathered K (before any
+                      //    update); 2 F and theta of the updated links (odd half-sweep)
+  int update;         // 0: read-only pass (with obs = 1): gather, no update, no store
+  double2* obs_site;  // [copy][site] (F, theta) contributions written by lane 0
 };
+
+// Per-site FP64 observables from the slot matrices M (M = U_mu(x) for up
+// slots, U_mu(x-mu)^dag for down slots).  K(x) = sum of the gathered slots,
+// so theta_site = tr[Delta Delta^dag] with Delta the traceless part of
+// (K - K^dag)/(2i) (Landau/Coulomb), or sum over subgroups |X_01|^2 with
+// X = sum of the blocks' W s3 W^dag (MAG); F_site sums Re tr M (Landau,
+// Coulomb) or |M_kk|^2 (MAG) over the slots.  Each lane adds its own slots in
+// FP64; an xor butterfly combines the lanes of the site.
+template <typename R, int GAUGE, int LPT>
+__device__ __forceinline__ void site_observables(const mat3<R> (&u)[LPT], const bool (&use)[LPT],
+                                                 const bool (&gather)[LPT], double& F, double& theta) {
+  constexpr int L = 8 / LPT;
+  F = 0.0;
+  theta = 0.0;
+  if (GAUGE == MAG) {
+    double xr[3] = {0, 0, 0}, xi[3] = {0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < LPT; ++j) {
+      if (!use[j]) continue;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        F += (double)u[j].e[k][k].re * u[j].e[k][k].re + (double)u[j].e[k][k].im * u[j].e[k][k].im;
+#pragma unroll
+      for (int sub = 0; sub < 3; ++sub) {
+        const int i = sub == 2 ? 1 : 0, i2 = sub == 0 ? 1 : 2;
+        const cx<R> A = u[j].e[i][i], B = u[j].e[i][i2], C = u[j].e[i2][i], D = u[j].e[i2][i2];
+        // A conj(C) - B conj(D), products exact in FP64 for FP32 inputs
+        xr[sub] += (double)A.re * C.re + (double)A.im * C.im - (double)B.re * D.re - (double)B.im * D.im;
+        xi[sub] += (double)A.im * C.re - (double)A.re * C.im - (double)B.im * D.re + (double)B.re * D.im;
+      }
+    }
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) {
+      F += __shfl_xor_sync(FULL, F, o);
+#pragma unroll
+      for (int sub = 0; sub < 3; ++sub) {
+        xr[sub] += __shfl_xor_sync(FULL, xr[sub], o);
+        xi[sub] += __shfl_xor_sync(FULL, xi[sub], o);
+      }
+    }
+#pragma unroll
+    for (int sub = 0; sub < 3; ++sub) theta += xr[sub] * xr[sub] + xi[sub] * xi[sub];
+  } else {
+    double kr[3][3], ki[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) kr[a][b] = ki[a][b] = 0.0;
+#pragma unroll
+    for (int j = 0; j < LPT; ++j) {
+      if (!(use[j] && gather[j])) continue;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          kr[a][b] += (double)u[j].e[a][b].re;
+          ki[a][b] += (double)u[j].e[a][b].im;
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1)
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          kr[a][b] += __shfl_xor_sync(FULL, kr[a][b], o);
+          ki[a][b] += __shfl_xor_sync(FULL, ki[a][b], o);
+        }
+    F = kr[0][0] + kr[1][1] + kr[2][2];
+    double dr[3][3], di[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        dr[a][b] = 0.5 * (ki[a][b] + ki[b][a]);
+        di[a][b] = -0.5 * (kr[a][b] - kr[b][a]);
+      }
+    const double tr3 = (dr[0][0] + dr[1][1] + dr[2][2]) / 3.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dr[a][a] -= tr3;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) theta += dr[a][b] * dr[a][b] + di[a][b] * di[a][b];
+  }
+}
 
 // Element offset of (copy, parity, slot, chunk 0, site index).
 __device__ __forceinline__ size_t link_off(uint32_t copy, int p, int slot, int NS, int NC, uint32_t Vh,
@@ -117,7 +207,7 @@ __device__ __forceinline__ void prefetch_tile(const SweepArgs<R>& a, uint32_t co
 // not gathered) and slot 1 is idle; the temporal links are not touched.
 // The grid is persistent over tiles of BLOCK/L sites; each block prefetches
 // its next tile into L2 while it works on the current one.
-template <typename R, int GAUGE, int ALGO, int LPT>
+template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
 __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy, uint32_t sp, bool valid,
                                            int lane) {
   constexpr int NC = store_traits<R>::NC;
@@ -162,11 +252,14 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
     }
   }
 
-  // mixed precision: the accumulated gauge transformation of this site
+  // mixed precision: the accumulated gauge transformation of this site (the
+  // FP32 working copy only, so FP64 kernels carry no code for it)
+  constexpr bool CAN_ACC = sizeof(R) == 4 && GAUGE != COULOMB;
+  const bool acc = CAN_ACC && a.acc;
   mat3<R> gacc;
   size_t acc_off = 0;
-  const bool use_acc = a.acc && valid && lane == 0;
-  if (a.acc) {
+  const bool use_acc = acc && valid && lane == 0;
+  if (acc) {
     if (use_acc) {
       acc_off = link_off(copy, a.parity, 4, a.NS, NC, Vh, sp);
       load_rows(a.links + acc_off, Vh, gacc);
@@ -177,6 +270,13 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
   }
 
   Rng rng{a.k0, a.k1, s, a.sweep, a.copy0 + copy};
+
+  if (OBS && a.obs == 1) {  // theta of the current links at this site (K as gathered)
+    double F, th;
+    site_observables<R, GAUGE, LPT>(u, use, gather, F, th);
+    if (valid && lane == 0) a.obs_site[(size_t)copy * G.V + s] = make_double2(0.0, th);
+  }
+  if (OBS && !a.update) return;
 
 #pragma unroll
   for (int sub = 0; sub < 3; ++sub) {
@@ -245,9 +345,14 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
     }
 #pragma unroll
     for (int j = 0; j < LPT; ++j) left_subgroup_mult(u[j], i, j2, g);
-    if (a.acc) left_subgroup_mult(gacc, i, j2, g);
+    if (acc) left_subgroup_mult(gacc, i, j2, g);
   }
   if (use_acc) store_rows(a.links + acc_off, Vh, gacc);
+  if (OBS && a.obs == 2) {  // F (every link is written once in a half-sweep) and theta after the update
+    double F, th;
+    site_observables<R, GAUGE, LPT>(u, use, gather, F, th);
+    if (valid && lane == 0) a.obs_site[(size_t)copy * G.V + s] = make_double2(F, th);
+  }
 
 #pragma unroll
   for (int j = 0; j < LPT; ++j) {
@@ -267,7 +372,9 @@ constexpr int min_blocks() {
                         : (LPT >= 4 ? 1 : LPT == 2 ? 2 : 3);
 }
 
-template <typename R, int GAUGE, int ALGO, int LPT>
+// OBS: the variant with the fused observables (used for overrelaxation check
+// sweeps only, so that the plain kernels keep their register budget).
+template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
 __global__ void __launch_bounds__(BLOCK, min_blocks<R, LPT>()) sweep_kernel(const SweepArgs<R> a) {
   constexpr int NC = store_traits<R>::NC;
   constexpr int L = 8 / LPT;
@@ -286,7 +393,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R, LPT>()) sweep_kernel(cons
     }
     const uint32_t copy = (uint32_t)(tile / tiles_per_copy);
     const uint32_t sp = (uint32_t)(tile - (uint64_t)copy * tiles_per_copy) * TILE + local;
-    sweep_site<R, GAUGE, ALGO, LPT>(a, copy, sp, sp < Vh, lane);
+    sweep_site<R, GAUGE, ALGO, LPT, OBS>(a, copy, sp, sp < Vh, lane);
   }
 }
 

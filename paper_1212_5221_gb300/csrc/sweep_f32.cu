@@ -21,15 +21,23 @@ static unsigned resident_blocks(K kernel) {
   return cached;
 }
 
-template <typename R, int GAUGE, int ALGO, int LPT>
-static cudaError_t launch_one(const SweepArgs<R>& a, cudaStream_t st) {
+template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
+static cudaError_t launch_kernel(const SweepArgs<R>& a, cudaStream_t st) {
   constexpr uint32_t TILE = BLOCK / (8 / LPT);
   const uint64_t ntiles = (uint64_t)((a.geom.Vh + TILE - 1) / TILE) * a.ncopies;
-  auto kernel = sweep_kernel<R, GAUGE, ALGO, LPT>;
+  auto kernel = sweep_kernel<R, GAUGE, ALGO, LPT, OBS>;
   const unsigned resident = resident_blocks(kernel);
   const unsigned blocks = (unsigned)((resident && ntiles > resident) ? resident : ntiles);
   kernel<<<blocks, BLOCK, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+// The fused-observables variant exists for overrelaxation only.
+template <typename R, int GAUGE, int ALGO, int LPT>
+static cudaError_t launch_one(const SweepArgs<R>& a, cudaStream_t st) {
+  if (a.obs == 0) return launch_kernel<R, GAUGE, ALGO, LPT, false>(a, st);
+  if constexpr (ALGO == ALG_OR) return launch_kernel<R, GAUGE, ALGO, LPT, true>(a, st);
+  return cudaErrorInvalidValue;
 }
 
 template <typename R, int GAUGE, int ALGO>

@@ -82,6 +82,7 @@ _SIG = {
     "gf_set_copy_base": [_P, ctypes.c_uint32],
     "gf_set_links_per_thread": [_P, _I],
     "gf_set_prefetch": [_P, _I],
+    "gf_set_fused_observables": [_P, _I],
     "gf_get_links_per_thread": [_P, _PI],
     "gf_autotune": [_P, _I, _PI, _PD],
     "gf_fix": [_P, ctypes.POINTER(gf_fix_params), ctypes.POINTER(gf_fix_result)],
@@ -285,6 +286,10 @@ def gf_set_links_per_thread(h, lpt):
 
 def gf_set_prefetch(h, on=True):
     _check(lib().gf_set_prefetch(h, 1 if on else 0), "gf_set_prefetch")
+
+
+def gf_set_fused_observables(h, on=True):
+    _check(lib().gf_set_fused_observables(h, 1 if on else 0), "gf_set_fused_observables")
 
 
 def gf_get_links_per_thread(h):

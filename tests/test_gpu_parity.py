@@ -183,6 +183,45 @@ def test_ten_sweeps_and_observables(gf, synth, orc, gauge, prec):
     assert abs(gF[0] - F) <= (1e-12 if prec == "fp64" else 1e-5) * abs(F)
 
 
+@pytest.mark.parametrize("lpt", [1, 4, 8])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("gauge", GAUGES)
+def test_fused_observables(gf, synth, orc, gauge, prec, lpt):
+    """F/theta fused into the last sweep equal the standalone pass and the oracle."""
+    U = rough(synth, orc, DIMS, 0.4, 5, 13)
+    W = U.copy()
+    orc.sweep(W, gauge, "or", 1.7, 3)
+    F, th, _, _ = orc.observables(W, gauge)
+    out = {}
+    for fused in (True, False):
+        with Ctx(gf, DIMS, gauge, prec) as h:
+            gf.gf_set_links_per_thread(h, lpt)
+            gf.gf_set_fused_observables(h, fused)
+            gf.gf_load_links(h, 0, U)
+            out[fused] = gf.gf_sweep(h, "or", 1.7, 3)
+            assert np.array_equal(out[fused][0], gf.gf_functional_theta(h)[0]) or fused
+            sF, sT = gf.gf_functional_theta(h)
+        assert abs(out[fused][0][0] - sF[0]) <= 1e-13 * abs(sF[0])
+        assert abs(out[fused][1][0] - sT[0]) <= 1e-12 * abs(sT[0])
+    rtol = 1e-12 if prec == "fp64" else 1e-5
+    assert abs(out[True][0][0] - F) <= rtol * abs(F)
+    assert abs(out[True][1][0] - th) <= (1e-11 if prec == "fp64" else 1e-3) * abs(th)
+
+
+def test_fix_fused_equals_standalone(gf, synth, orc):
+    U = synth.links((8, 8, 8, 8), "smooth", 0.3, 0)
+    orc.random_gauge_transform(U, 100)
+    res = {}
+    for fused in (True, False):
+        with Ctx(gf, (8, 8, 8, 8), "landau", "fp64") as h:
+            gf.gf_set_fused_observables(h, fused)
+            gf.gf_load_links(h, 0, U)
+            r = gf.gf_fix(h, "or", 1.7, 1e-12, check_interval=10)
+            res[fused] = (r["sweeps"], gf.gf_functional_theta(h))
+    assert res[True][0] == res[False][0]
+    assert np.array_equal(res[True][1][0], res[False][1][0])
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_reunitarize(gf, synth, orc, prec):
     U = rough(synth, orc, DIMS)
