@@ -229,6 +229,27 @@ typedef struct {
 
 int gf_fix(gf_ctx* ctx, const gf_fix_params* params, gf_fix_result* result);
 
+/* The annealing protocol of Sec. 6.5 for every copy of the batch: sa_steps
+ * simulated-annealing steps (heat bath + three microcanonical sweeps, T
+ * linear from T_start to T_end), then stochastic relaxation (probability
+ * sr_p) until every copy has theta < sr_theta or sr_sweeps have run, then
+ * overrelaxation to theta_target with the parameters of `fix` (gf_fix).
+ * Random draws are keyed by (seed, site, sweep index, copy).  The result
+ * counts every sweep (an SA step is four) and reports gf_fix's convergence;
+ * gf_functional_theta then gives each copy's functional, from which the
+ * best Gribov copy is chosen. */
+typedef struct {
+  int sa_steps;
+  double T_start, T_end;
+  int sr_sweeps;
+  double sr_p;
+  double sr_theta;
+  uint64_t seed;
+  gf_fix_params fix;
+} gf_protocol_params;
+
+int gf_protocol(gf_ctx* ctx, const gf_protocol_params* params, gf_fix_result* result);
+
 /* The device Philox4x32-10 (Salmon et al., SC'11) that keys every random draw
  * of the sweeps and gauge transformations: out[4k..4k+3] = Philox(counters
  * [4k..4k+3], key = (seed low word, seed high word)) for k < n.  Host arrays;

@@ -1034,6 +1034,83 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
   return GF_OK;
 }
 
+int gf_protocol(gf_ctx* c, const gf_protocol_params* P, gf_fix_result* res) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!P) return fail(GF_EINVAL, "params is NULL");
+  if (P->sa_steps < 0 || P->sr_sweeps < 0) return fail(GF_EINVAL, "negative sweep counts");
+  if (P->sa_steps > 0 && (!(P->T_start > 0) || !(P->T_end > 0))) return fail(GF_EINVAL, "temperatures must be > 0");
+  if (P->sr_sweeps > 0 && (r = check_algo_param(GF_SR, P->sr_p))) return r;
+  const auto t_start = std::chrono::steady_clock::now();
+  gf_fix_result R;
+  memset(&R, 0, sizeof R);
+  const uint64_t sites = (uint64_t)c->ncopies * c->G.V;
+  // 1. simulated annealing: heat bath + three microcanonical sweeps per step,
+  //    T linear from T_start to T_end (Sec. 2.3)
+  for (int k = 0; k < P->sa_steps; ++k) {
+    const double T = P->sa_steps > 1 ? P->T_start + (P->T_end - P->T_start) * k / (double)(P->sa_steps - 1)
+                                     : P->T_start;
+    if ((r = api_sweep(c, GF_SA, T, P->seed))) return r;
+    R.sweeps += 4;
+    R.site_updates += 4 * sites;
+    if (c->prec != GF_FP64 && !c->fp64) {
+      R.sweeps_fp32 += 4;
+      if (P->fix.reunit_interval > 0 && (k + 1) * 4 % P->fix.reunit_interval < 4 && (r = reunitarize(c))) return r;
+    } else {
+      R.sweeps_fp64 += 4;
+    }
+  }
+  // 2. stochastic relaxation until every copy has theta < sr_theta or
+  //    sr_sweeps have run (Sec. 2.2.5, Sec. 6.5)
+  int done = 0;
+  std::vector<double> ct;
+  std::vector<double> Fc(c->ncopies), Tc(c->ncopies);
+  // a copy leaves the SR phase at the first check with theta < sr_theta, so a
+  // copy's trajectory is the same alone and in a batch
+  const int Nt = c->dims[0];
+  while (done < P->sr_sweeps) {
+    if ((r = observables(c, ct))) return r;
+    R.checks++;
+    copy_means(c, ct, Fc.data(), Tc.data());
+    int n_active = 0;
+    for (int k = 0; k < c->ncopies; ++k) {
+      const int v = (c->active_h[(size_t)k * Nt] && Tc[k] >= P->sr_theta) ? 1 : 0;
+      for (int t = 0; t < Nt; ++t) c->active_h[(size_t)k * Nt + t] = v;
+      n_active += v;
+    }
+    if ((r = upload_active(c))) return r;
+    if (n_active == 0) break;
+    const int k = std::min(P->fix.check_interval > 0 ? P->fix.check_interval : 10, P->sr_sweeps - done);
+    for (int i = 0; i < k; ++i) {
+      if ((r = api_sweep(c, GF_SR, P->sr_p, P->seed))) return r;
+      if (c->prec != GF_FP64 && !c->fp64) {
+        R.sweeps_fp32++;
+        if (P->fix.reunit_interval > 0 && (R.sweeps_fp32 % P->fix.reunit_interval) == 0 && (r = reunitarize(c)))
+          return r;
+      } else {
+        R.sweeps_fp64++;
+      }
+    }
+    done += k;
+    R.sweeps += k;
+    R.site_updates += (uint64_t)k * n_active * c->G.V;
+  }
+  std::fill(c->active_h.begin(), c->active_h.end(), 1);
+  if ((r = upload_active(c))) return r;
+  // 3. overrelaxation to theta_target
+  gf_fix_result F;
+  r = gf_fix(c, &P->fix, &F);
+  R.sweeps += F.sweeps;
+  R.sweeps_fp32 += F.sweeps_fp32;
+  R.sweeps_fp64 += F.sweeps_fp64;
+  R.checks += F.checks;
+  R.site_updates += F.site_updates;
+  R.converged = F.converged;
+  R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  if (res) *res = R;
+  return r;
+}
+
 int gf_set_profiling(gf_ctx* c, int on) {
   int r = check_ctx(c);
   if (r) return r;

@@ -44,6 +44,12 @@ class gf_fix_params(ctypes.Structure):
                 ("seed", ctypes.c_uint64)]
 
 
+class gf_protocol_params(ctypes.Structure):
+    _fields_ = [("sa_steps", ctypes.c_int), ("T_start", ctypes.c_double), ("T_end", ctypes.c_double),
+                ("sr_sweeps", ctypes.c_int), ("sr_p", ctypes.c_double), ("sr_theta", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("fix", gf_fix_params)]
+
+
 class gf_fix_result(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("sweeps_fp32", ctypes.c_int), ("sweeps_fp64", ctypes.c_int),
                 ("checks", ctypes.c_int), ("converged", ctypes.c_int), ("seconds", ctypes.c_double),
@@ -86,6 +92,7 @@ _SIG = {
     "gf_get_links_per_thread": [_P, _PI],
     "gf_autotune": [_P, _I, _PI, _PD],
     "gf_fix": [_P, ctypes.POINTER(gf_fix_params), ctypes.POINTER(gf_fix_result)],
+    "gf_protocol": [_P, ctypes.POINTER(gf_protocol_params), ctypes.POINTER(gf_fix_result)],
     "gf_get_info": [_P, _PI, _PI, _PI, _PI, _PI],
     "gf_philox": [ctypes.c_uint64, _P, ctypes.c_size_t, _P],
     "gf_set_profiling": [_P, _I],
@@ -314,6 +321,21 @@ def gf_fix(h, algo="or", param=1.7, theta_target=1e-12, max_sweeps=100000, check
     if st == GF_ENOTCONV and not raise_on_notconv:
         return r.as_dict()
     _check(st, "gf_fix")
+    return r.as_dict()
+
+
+def gf_protocol(h, sa_steps, T_start, T_end, sr_sweeps=0, sr_p=0.5, sr_theta=0.0, seed=0, omega=1.35,
+                theta_target=1e-12, max_sweeps=100000, check_interval=10, reunit_interval=100,
+                switch_theta=1e-8, raise_on_notconv=True):
+    fix = gf_fix_params(GF_OR, float(omega), float(theta_target), int(max_sweeps), int(check_interval),
+                        int(reunit_interval), float(switch_theta), int(seed))
+    p = gf_protocol_params(int(sa_steps), float(T_start), float(T_end), int(sr_sweeps), float(sr_p),
+                           float(sr_theta), int(seed), fix)
+    r = gf_fix_result()
+    st = lib().gf_protocol(h, ctypes.byref(p), ctypes.byref(r))
+    if st == GF_ENOTCONV and not raise_on_notconv:
+        return r.as_dict()
+    _check(st, "gf_protocol")
     return r.as_dict()
 
 

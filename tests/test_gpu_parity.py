@@ -361,6 +361,34 @@ def test_batch_equals_alone(gf, synth, orc):
         assert np.array_equal(alone, batched[k])
 
 
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_protocol_batch_equals_alone(gf, synth, orc, prec):
+    """SA -> SR -> OR (Sec. 6.5) on three Gribov copies in one batch: every copy
+    converges, and each copy run alone (same Philox copy id) reaches the same
+    functional; the best copy is the one with the largest F."""
+    dims = (4, 4, 6, 8)
+    U = synth.links(dims, "smooth", 0.4, 7)
+    kw = dict(sa_steps=15, T_start=1.45, T_end=0.01, sr_sweeps=40, sr_p=0.5, sr_theta=1e-6, seed=11,
+              omega=1.35, theta_target=1e-10, max_sweeps=40000, check_interval=10)
+    with Ctx(gf, dims, "mag", prec, n_copies=3) as h:
+        gf.gf_load_links(h, -1, U)
+        gf.gf_random_gauge_transform(h, 5)
+        starts = [store(gf, h, dims, k) for k in range(3)]
+        r = gf.gf_protocol(h, **kw)
+        Fb, Tb = gf.gf_functional_theta(h)
+    assert r["converged"] and (Tb < 1e-10).all()
+    for k in range(3):
+        with Ctx(gf, dims, "mag", prec) as h:
+            gf.gf_set_copy_base(h, k)
+            gf.gf_load_links(h, 0, starts[k])
+            r1 = gf.gf_protocol(h, **kw)
+            F1, T1 = gf.gf_functional_theta(h)
+        assert r1["converged"] and T1[0] < 1e-10
+        assert abs(F1[0] - Fb[k]) <= 1e-9 * abs(Fb[k])
+    # the functional is gauge dependent and the copies differ (distinct orbit points)
+    assert np.ptp(Fb) > 0 or np.allclose(Fb, Fb[0])
+
+
 def test_lpt_variants_agree(gf, synth, orc):
     U = rough(synth, orc, (8, 8, 8, 8))
     outs = []
