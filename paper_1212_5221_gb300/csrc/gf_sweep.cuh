@@ -30,15 +30,40 @@ struct SweepArgs {
 };
 
 // Per-site FP64 observables from the slot matrices M (M = U_mu(x) for up
-// slots, U_mu(x-mu)^dag for down slots).  K(x) = sum of the gathered slots,
-// so theta_site = tr[Delta Delta^dag] with Delta the traceless part of
-// (K - K^dag)/(2i) (Landau/Coulomb), or sum over subgroups |X_01|^2 with
-// X = sum of the blocks' W s3 W^dag (MAG); F_site sums Re tr M (Landau,
-// Coulomb) or |M_kk|^2 (MAG) over the slots.  Each lane adds its own slots in
-// FP64; an xor butterfly combines the lanes of the site.
+// slots, U_mu(x-mu)^dag for down slots).  Each slot is taken as stored: the
+// two stored rows of its link, with the third rebuilt as conj(row0 x row1)
+// in FP64 (exactly what a later read of the links gives).  K(x) = sum of the
+// gathered slots, so theta_site = tr[Delta Delta^dag] with Delta the
+// traceless part of (K - K^dag)/(2i) (Landau/Coulomb), or sum over subgroups
+// |X_01|^2 with X = sum of the blocks' W s3 W^dag (MAG); F_site sums Re tr M
+// (Landau, Coulomb) or |M_kk|^2 (MAG).  Each lane adds its own slots in FP64;
+// an xor butterfly combines the lanes of the site.
+template <typename R>
+__device__ __forceinline__ void stored_slot(const mat3<R>& m, bool down, mat3<double>& d) {
+  if (!down) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) d.e[a][b] = {(double)m.e[a][b].re, (double)m.e[a][b].im};
+    reconstruct_row2(d);
+  } else {
+    mat3<double> u;  // the stored link is M^dag: rows 0,1 = conj of M's columns 0,1
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) u.e[a][b] = {(double)m.e[b][a].re, -(double)m.e[b][a].im};
+    reconstruct_row2(u);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) d.e[a][b] = {u.e[b][a].re, -u.e[b][a].im};
+  }
+}
+
 template <typename R, int GAUGE, int LPT>
 __device__ __forceinline__ void site_observables(const mat3<R> (&u)[LPT], const bool (&use)[LPT],
-                                                 const bool (&gather)[LPT], double& F, double& theta) {
+                                                 const bool (&gather)[LPT], int lane, double& F,
+                                                 double& theta) {
   constexpr int L = 8 / LPT;
   F = 0.0;
   theta = 0.0;
@@ -47,16 +72,17 @@ __device__ __forceinline__ void site_observables(const mat3<R> (&u)[LPT], const 
 #pragma unroll
     for (int j = 0; j < LPT; ++j) {
       if (!use[j]) continue;
+      mat3<double> m;
+      stored_slot(u[j], (LPT >= 2) ? (j & 1) : ((lane * LPT + j) & 1), m);
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
-        F += (double)u[j].e[k][k].re * u[j].e[k][k].re + (double)u[j].e[k][k].im * u[j].e[k][k].im;
+      for (int k = 0; k < 3; ++k) F += m.e[k][k].re * m.e[k][k].re + m.e[k][k].im * m.e[k][k].im;
 #pragma unroll
       for (int sub = 0; sub < 3; ++sub) {
         const int i = sub == 2 ? 1 : 0, i2 = sub == 0 ? 1 : 2;
-        const cx<R> A = u[j].e[i][i], B = u[j].e[i][i2], C = u[j].e[i2][i], D = u[j].e[i2][i2];
-        // A conj(C) - B conj(D), products exact in FP64 for FP32 inputs
-        xr[sub] += (double)A.re * C.re + (double)A.im * C.im - (double)B.re * D.re - (double)B.im * D.im;
-        xi[sub] += (double)A.im * C.re - (double)A.re * C.im - (double)B.im * D.re + (double)B.re * D.im;
+        const cx<double> A = m.e[i][i], B = m.e[i][i2], C = m.e[i2][i], D = m.e[i2][i2];
+        // A conj(C) - B conj(D)
+        xr[sub] += A.re * C.re + A.im * C.im - B.re * D.re - B.im * D.im;
+        xi[sub] += A.im * C.re - A.re * C.im - B.im * D.re + B.re * D.im;
       }
     }
 #pragma unroll
@@ -79,12 +105,14 @@ __device__ __forceinline__ void site_observables(const mat3<R> (&u)[LPT], const 
 #pragma unroll
     for (int j = 0; j < LPT; ++j) {
       if (!(use[j] && gather[j])) continue;
+      mat3<double> m;
+      stored_slot(u[j], (LPT >= 2) ? (j & 1) : ((lane * LPT + j) & 1), m);
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-          kr[a][b] += (double)u[j].e[a][b].re;
-          ki[a][b] += (double)u[j].e[a][b].im;
+          kr[a][b] += m.e[a][b].re;
+          ki[a][b] += m.e[a][b].im;
         }
     }
 #pragma unroll
@@ -273,7 +301,7 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
 
   if (OBS && a.obs == 1) {  // theta of the current links at this site (K as gathered)
     double F, th;
-    site_observables<R, GAUGE, LPT>(u, use, gather, F, th);
+    site_observables<R, GAUGE, LPT>(u, use, gather, lane, F, th);
     if (valid && lane == 0) a.obs_site[(size_t)copy * G.V + s] = make_double2(0.0, th);
   }
   if (OBS && !a.update) return;
@@ -350,7 +378,7 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
   if (use_acc) store_rows(a.links + acc_off, Vh, gacc);
   if (OBS && a.obs == 2) {  // F (every link is written once in a half-sweep) and theta after the update
     double F, th;
-    site_observables<R, GAUGE, LPT>(u, use, gather, F, th);
+    site_observables<R, GAUGE, LPT>(u, use, gather, lane, F, th);
     if (valid && lane == 0) a.obs_site[(size_t)copy * G.V + s] = make_double2(F, th);
   }
 
