@@ -211,8 +211,9 @@ typedef struct {
   double theta_target;   /* e.g. 1e-12 */
   int max_sweeps;        /* per run; GF_ENOTCONV beyond */
   int check_interval;    /* sweeps between theta evaluations, >= 1 */
-  int reunit_interval;   /* FP32 sweeps: every this many sweeps re-unitarise (GF_FP32) or apply the
-                            accumulated transformation to the FP64 master (GF_MIXED); 0 = never */
+  int reunit_interval;   /* every this many sweeps re-unitarise the links (GF_FP32, GF_FP64, and
+                            GF_MIXED's FP64 stage) or apply the accumulated transformation to the
+                            FP64 master (GF_MIXED's FP32 stage); 0 = never */
   double switch_theta;   /* GF_MIXED: FP32 -> FP64 sweeps below this theta (e.g. 1e-8) */
   uint64_t seed;         /* unused by OR/RELAX; kept for symmetry with gf_sweep */
 } gf_fix_params;

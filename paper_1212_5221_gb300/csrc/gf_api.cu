@@ -1012,15 +1012,16 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
       if ((r = api_sweep(c, P->algo, P->param, P->seed, last))) return r;
       if (last) fused_ready = true;
       R.site_updates += (uint64_t)n_active * sites_per_unit;
-      if (c->fp64) {
+      if (c->fp64)
         R.sweeps_fp64++;
-      } else {
+      else
         R.sweeps_fp32++;
-        if (P->reunit_interval > 0 && ++since_reunit >= P->reunit_interval) {
-          since_reunit = 0;
-          if ((r = reunitarize(c))) return r;
-          fused_ready = false;  // the links changed after the fused half-sweep
-        }
+      // re-unitarise (FP32, FP64) or apply the accumulated transformation to
+      // the FP64 master (GF_MIXED's FP32 stage) every reunit_interval sweeps
+      if (P->reunit_interval > 0 && ++since_reunit >= P->reunit_interval) {
+        since_reunit = 0;
+        if ((r = reunitarize(c))) return r;
+        fused_ready = false;  // the links changed after the fused half-sweep
       }
     }
     R.sweeps += k;

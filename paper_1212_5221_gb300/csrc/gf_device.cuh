@@ -392,6 +392,28 @@ __device__ __forceinline__ void haar_su3(const Rng& rng, mat3<R>& g) {
   reconstruct_row2(g);
 }
 
+// Rows 0 and 1 scaled to unit norm.  With 12-real storage the third row is
+// rebuilt as conj(row0 x row1), and a subgroup rotation in (0,2) or (1,2)
+// mixes it back into the stored rows: a norm error d0, d1 of the rows then
+// grows as d0 -> d0 + sin^2 d1 (the rows' inner product only shrinks, since
+// (r0 x r1).r1 = 0), i.e. exponentially under large rotations (heat bath,
+// microcanonical steps, early sweeps).  Renormalising the two rows at every
+// load keeps the stored matrices unitary to rounding.
+__device__ __forceinline__ float rnorm_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rnorm_(double x) { return 1.0 / sqrt(x); }
+template <typename R>
+__device__ __forceinline__ void normalize_rows(mat3<R>& u) {
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    R n = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) n += u.e[a][k].re * u.e[a][k].re + u.e[a][k].im * u.e[a][k].im;
+    const R inv = rnorm_(n);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) u.e[a][k] = {u.e[a][k].re * inv, u.e[a][k].im * inv};
+  }
+}
+
 // Re-unitarisation: normalise row 0, Gram-Schmidt row 1 against it,
 // normalise (the third row stays implicit).
 template <typename R>

@@ -384,9 +384,36 @@ def test_protocol_batch_equals_alone(gf, synth, orc, prec):
             r1 = gf.gf_protocol(h, **kw)
             F1, T1 = gf.gf_functional_theta(h)
         assert r1["converged"] and T1[0] < 1e-10
-        assert abs(F1[0] - Fb[k]) <= 1e-9 * abs(Fb[k])
+        # batch and alone stop at different checks; at theta < 1e-10 that moves F
+        # by O(1e-9) (the same Gribov copy)
+        assert abs(F1[0] - Fb[k]) <= 2e-8 * abs(Fb[k])
     # the functional is gauge dependent and the copies differ (distinct orbit points)
     assert np.ptp(Fb) > 0 or np.allclose(Fb, Fb[0])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "mixed"])
+@pytest.mark.parametrize("gauge,algo", [("landau", "sa"), ("mag", "sa"), ("mag", "micro"), ("landau", "sr")])
+def test_long_large_rotation_runs_stay_unitary(gf, synth, orc, gauge, algo, prec):
+    """With 12-real storage the rebuilt third row feeds norm errors back into the
+    stored rows under large rotations; without renormalisation at load, 50
+    heat-bath steps turned every link into NaN.  300 sweeps must stay unitary."""
+    dims = (8, 8, 8, 8)
+    U = rough(synth, orc, dims, 0.3, 3, 4)
+    with Ctx(gf, dims, gauge, prec) as h:
+        gf.gf_load_links(h, 0, U)
+        if algo == "sa":
+            gf.gf_anneal(h, 1.45, 0.5, 75, 4, observables=False)  # 300 sweeps
+        else:
+            gf.gf_sweep(h, algo, 0.5, 300, 4, observables=False)
+        F, T = gf.gf_functional_theta(h)
+        V = store(gf, h, dims)
+    assert np.isfinite(V).all() and np.isfinite(F).all() and np.isfinite(T).all()
+    M = V.reshape(-1, 3, 3)
+    dev = np.abs(M @ M.conj().transpose(0, 2, 1) - np.eye(3)).max()
+    assert dev < (1e-13 if prec in ("fp64", "mixed") else 2e-6), dev
+    if algo == "micro":  # microcanonical sweeps keep the functional (Sec. 2.2.4)
+        F0 = orc.observables(U, gauge)[0]
+        assert abs(F[0] - F0) < (1e-12 if prec == "fp64" else 1e-4)
 
 
 def test_lpt_variants_agree(gf, synth, orc):
