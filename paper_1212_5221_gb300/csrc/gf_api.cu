@@ -990,7 +990,10 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
         best_fp32 = worst;
         best_at = R.sweeps;
       }
-      const bool stalled = R.sweeps - best_at >= 25 * P->check_interval;
+      // FP32 "stalls" only near its rounding floor: far above it, slow progress
+      // (MAG) is just slow convergence, and FP32 sweeps are the faster way on
+      const bool stalled = worst < std::max(100.0 * P->switch_theta, 1e-9) &&
+                           R.sweeps - best_at >= 25 * P->check_interval;
       if (worst < P->switch_theta || stalled || !std::isfinite(worst)) {
         if ((r = promote(c))) return r;
         prev_worst = -1.0;

@@ -392,26 +392,40 @@ __device__ __forceinline__ void haar_su3(const Rng& rng, mat3<R>& g) {
   reconstruct_row2(g);
 }
 
-// Rows 0 and 1 scaled to unit norm.  With 12-real storage the third row is
-// rebuilt as conj(row0 x row1), and a subgroup rotation in (0,2) or (1,2)
+// Re-projection of the two stored rows at load: row 0 normalised, row 1
+// made orthogonal to it and normalised.  With 12-real storage the third row
+// is rebuilt as conj(row0 x row1), and a subgroup rotation in (0,2) or (1,2)
 // mixes it back into the stored rows: a norm error d0, d1 of the rows then
-// grows as d0 -> d0 + sin^2 d1 (the rows' inner product only shrinks, since
-// (r0 x r1).r1 = 0), i.e. exponentially under large rotations (heat bath,
-// microcanonical steps, early sweeps).  Renormalising the two rows at every
-// load keeps the stored matrices unitary to rounding.
+// grows as d0 -> d0 + sin^2 d1, i.e. exponentially under large rotations
+// (heat bath, microcanonical steps, early sweeps), and rounding kicks
+// accumulate in the rows' inner product.  Re-projecting at every load keeps
+// the stored matrices unitary to rounding.
 __device__ __forceinline__ float rnorm_(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rnorm_(double x) { return 1.0 / sqrt(x); }
 template <typename R>
-__device__ __forceinline__ void normalize_rows(mat3<R>& u) {
+__device__ __forceinline__ void reproject_rows(mat3<R>& u) {
+  R n0 = 0;
 #pragma unroll
-  for (int a = 0; a < 2; ++a) {
-    R n = 0;
+  for (int k = 0; k < 3; ++k) n0 += u.e[0][k].re * u.e[0][k].re + u.e[0][k].im * u.e[0][k].im;
+  const R i0 = rnorm_(n0);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) n += u.e[a][k].re * u.e[a][k].re + u.e[a][k].im * u.e[a][k].im;
-    const R inv = rnorm_(n);
+  for (int k = 0; k < 3; ++k) u.e[0][k] = {u.e[0][k].re * i0, u.e[0][k].im * i0};
+  cx<R> ip{R(0), R(0)};  // <row0, row1>
 #pragma unroll
-    for (int k = 0; k < 3; ++k) u.e[a][k] = {u.e[a][k].re * inv, u.e[a][k].im * inv};
+  for (int k = 0; k < 3; ++k) {
+    ip.re += u.e[0][k].re * u.e[1][k].re + u.e[0][k].im * u.e[1][k].im;
+    ip.im += u.e[0][k].re * u.e[1][k].im - u.e[0][k].im * u.e[1][k].re;
   }
+  R n1 = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const cx<R> p = cmul(ip, u.e[0][k]);
+    u.e[1][k] = {u.e[1][k].re - p.re, u.e[1][k].im - p.im};
+    n1 += u.e[1][k].re * u.e[1][k].re + u.e[1][k].im * u.e[1][k].im;
+  }
+  const R i1 = rnorm_(n1);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) u.e[1][k] = {u.e[1][k].re * i1, u.e[1][k].im * i1};
 }
 
 // Re-unitarisation: normalise row 0, Gram-Schmidt row 1 against it,

@@ -249,11 +249,11 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
     if (a.active && !a.active[(size_t)copy * G.n[0] + c[0]]) valid = false;
   }
 
-  // rows renormalised at load (see normalize_rows): every FP32 kernel, and the
+  // rows re-projected at load (see reproject_rows): every FP32 kernel, and the
   // FP64 kernels whose rotations stay large (heat bath, microcanonical, SR);
   // FP64 overrelaxation converges to small rotations and is re-unitarised
-  // periodically by the driver instead.
-  constexpr bool NORM = sizeof(R) == 4 || ALGO != ALG_OR;
+  // periodically by the driver instead.  A read-only pass leaves them as stored.
+  const bool NORM = (sizeof(R) == 4 || ALGO != ALG_OR) && (!OBS || a.update);
   mat3<R> u[LPT];
   size_t off[LPT];
   bool use[LPT], gather[LPT];
@@ -278,7 +278,7 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
     off[j] = link_off(copy, par, slot, a.NS, NC, Vh, ssp);
     if (use[j]) {
       load_rows(a.links + off[j], Vh, u[j]);
-      if (NORM) normalize_rows(u[j]);
+      if (NORM) reproject_rows(u[j]);
       reconstruct_row2(u[j]);
       if (down) dagger(u[j]);
     } else {
@@ -297,7 +297,7 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
     if (use_acc) {
       acc_off = link_off(copy, a.parity, 4, a.NS, NC, Vh, sp);
       load_rows(a.links + acc_off, Vh, gacc);
-      normalize_rows(gacc);
+      reproject_rows(gacc);
       reconstruct_row2(gacc);
     } else {
       set_identity(gacc);
