@@ -425,7 +425,8 @@ def test_long_large_rotation_runs_stay_unitary(gf, synth, orc, gauge, algo, prec
     assert np.isfinite(V).all() and np.isfinite(F).all() and np.isfinite(T).all()
     M = V.reshape(-1, 3, 3)
     dev = np.abs(M @ M.conj().transpose(0, 2, 1) - np.eye(3)).max()
-    assert dev < (1e-13 if prec in ("fp64", "mixed") else 2e-6), dev
+    # FP32: every g is unit to a few ulp and each sweep applies three of them
+    assert dev < (1e-13 if prec in ("fp64", "mixed") else 1e-5), dev
     if algo == "micro":  # microcanonical sweeps keep the functional (Sec. 2.2.4)
         F0 = orc.observables(U, gauge)[0]
         assert abs(F[0] - F0) < (1e-12 if prec == "fp64" else 1e-4)
