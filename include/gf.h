@@ -300,6 +300,61 @@ int gf_launch_count(gf_ctx* ctx, uint64_t* n);
 int gf_functional_theta_noalloc(const int dims[4], gf_gauge gauge, const double* device_links, void* stream,
                                 double* F, double* theta, double* F_t, double* theta_t);
 
+/* Job server: many gauge-fixing jobs (different lattices, gauges and
+ * precisions) share the GPU.  gf_server_create reserves hbm_bytes of device
+ * memory once and starts `slots` worker threads.  A submitted job waits in a
+ * FIFO queue; it is admitted as soon as a slot is free and its footprint
+ * (gf_footprint) fits in the arena (a job that does not fit yet lets smaller
+ * jobs behind it go first, up to 4 x slots times).  Each admitted job gets its
+ * own context and CUDA stream carved from the arena (no cudaMalloc), so the
+ * kernels of concurrent jobs overlap; when it finishes, its slot and memory
+ * go to the next job.  A job: load host_links (natural order; the caller keeps
+ * the array alive until the job's result is polled), apply
+ * gf_random_gauge_transform(orbit_seed) unless orbit_seed is 0, run gf_fix
+ * with `fix`, then report F/theta and, if host_out is given, store the links
+ * there.  Times are seconds since the server was created. */
+typedef struct gf_server gf_server;
+
+typedef struct {
+  int dims[4];
+  gf_gauge gauge;
+  gf_precision prec;
+  const double* host_links;
+  uint64_t orbit_seed;
+  gf_fix_params fix;
+  double* host_out;
+  uint64_t tag;          /* returned with the result */
+} gf_job;
+
+typedef struct {
+  uint64_t tag;
+  int status;            /* GF_OK, GF_ENOTCONV, or an error code */
+  double F, theta;
+  int sweeps, sweeps_fp32, sweeps_fp64;
+  uint64_t site_updates;
+  size_t footprint;      /* arena bytes the job held */
+  double t_submit, t_admit, t_done;
+} gf_job_result;
+
+int gf_server_create(size_t hbm_bytes, int slots, gf_server** out);
+
+/* A test double with the same queue, admission and arena logic that runs
+ * no device code: each job just holds its memory for seconds_per_gb per GB
+ * of footprint. */
+int gf_server_create_mock(size_t hbm_bytes, int slots, double seconds_per_gb, gf_server** out);
+
+/* GF_ENOMEM if the job's footprint exceeds the whole arena. */
+int gf_server_submit(gf_server* server, const gf_job* job);
+
+/* Up to max_results finished jobs (in completion order), waiting up to
+ * wait_ms for the first one; *n_out receives the number returned. */
+int gf_server_poll(gf_server* server, gf_job_result* out, int max_results, int wait_ms, int* n_out);
+
+int gf_server_status(gf_server* server, int* queued, int* running, uint64_t* completed, size_t* bytes_in_use);
+
+/* Runs every queued job to completion, then releases the arena. */
+void gf_server_destroy(gf_server* server);
+
 /* Geometry and state queries. */
 int gf_get_info(gf_ctx* ctx, int dims[4], int* n_copies, int* gauge, int* precision, int* storage_fp64);
 

@@ -50,6 +50,23 @@ class gf_protocol_params(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("fix", gf_fix_params)]
 
 
+class gf_job(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4), ("gauge", ctypes.c_int), ("prec", ctypes.c_int),
+                ("host_links", ctypes.c_void_p), ("orbit_seed", ctypes.c_uint64), ("fix", gf_fix_params),
+                ("host_out", ctypes.c_void_p), ("tag", ctypes.c_uint64)]
+
+
+class gf_job_result(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int), ("F", ctypes.c_double),
+                ("theta", ctypes.c_double), ("sweeps", ctypes.c_int), ("sweeps_fp32", ctypes.c_int),
+                ("sweeps_fp64", ctypes.c_int), ("site_updates", ctypes.c_uint64),
+                ("footprint", ctypes.c_size_t), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class gf_fix_result(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("sweeps_fp32", ctypes.c_int), ("sweeps_fp64", ctypes.c_int),
                 ("checks", ctypes.c_int), ("converged", ctypes.c_int), ("seconds", ctypes.c_double),
@@ -99,6 +116,11 @@ _SIG = {
     "gf_kernel_stats": [_P, _I, ctypes.POINTER(ctypes.c_uint64), _PD],
     "gf_launch_count": [_P, ctypes.POINTER(ctypes.c_uint64)],
     "gf_functional_theta_noalloc": [_PI, _I, _P, _P, _P, _P, _P, _P],
+    "gf_server_create": [ctypes.c_size_t, _I, ctypes.POINTER(_P)],
+    "gf_server_create_mock": [ctypes.c_size_t, _I, _D, ctypes.POINTER(_P)],
+    "gf_server_submit": [_P, ctypes.POINTER(gf_job)],
+    "gf_server_poll": [_P, _P, _I, _I, _PI],
+    "gf_server_status": [_P, _PI, _PI, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_size_t)],
 }
 _lib = None
 
@@ -116,6 +138,8 @@ def lib():
             f.restype = _I
         L.gf_destroy.argtypes = [_P]
         L.gf_destroy.restype = None
+        L.gf_server_destroy.argtypes = [_P]
+        L.gf_server_destroy.restype = None
         L.gf_strerror.argtypes = [_I]
         L.gf_strerror.restype = ctypes.c_char_p
         L.gf_last_error.argtypes = []
@@ -375,6 +399,57 @@ def gf_functional_theta_noalloc(dims, gauge, device_links_ptr: int, stream=None)
                                              ctypes.byref(F), ctypes.byref(T), Ft.ctypes.data, Tt.ctypes.data),
            "gf_functional_theta_noalloc")
     return F.value, T.value, Ft, Tt
+
+
+def gf_server_create(hbm_bytes, slots):
+    h = _P()
+    _check(lib().gf_server_create(int(hbm_bytes), int(slots), ctypes.byref(h)), "gf_server_create")
+    return h
+
+
+def gf_server_create_mock(hbm_bytes, slots, seconds_per_gb):
+    h = _P()
+    _check(lib().gf_server_create_mock(int(hbm_bytes), int(slots), float(seconds_per_gb), ctypes.byref(h)),
+           "gf_server_create_mock")
+    return h
+
+
+def gf_server_submit(s, dims, gauge="landau", prec="mixed", host_links=None, orbit_seed=0, tag=0,
+                     host_out=None, algo="or", param=1.7, theta_target=1e-12, max_sweeps=100000,
+                     check_interval=20, reunit_interval=100, switch_theta=1e-8):
+    """Queue a job; host_links / host_out (numpy complex128, natural order) must stay
+    alive until the job's result has been polled."""
+    j = gf_job()
+    j.dims[:] = [int(d) for d in dims]
+    j.gauge = _enum(gauge, GAUGES)
+    j.prec = _enum(prec, PRECISIONS)
+    j.host_links = None if host_links is None else _links_arg(host_links)
+    j.orbit_seed = int(orbit_seed)
+    j.fix = gf_fix_params(_enum(algo, ALGOS), float(param), float(theta_target), int(max_sweeps),
+                          int(check_interval), int(reunit_interval), float(switch_theta), 0)
+    j.host_out = None if host_out is None else _links_arg(host_out)
+    j.tag = int(tag)
+    _check(lib().gf_server_submit(s, ctypes.byref(j)), "gf_server_submit")
+
+
+def gf_server_poll(s, max_results=64, wait_ms=0):
+    arr = (gf_job_result * max_results)()
+    n = ctypes.c_int()
+    _check(lib().gf_server_poll(s, arr, max_results, int(wait_ms), ctypes.byref(n)), "gf_server_poll")
+    return [arr[k].as_dict() for k in range(n.value)]
+
+
+def gf_server_status(s):
+    q, r = ctypes.c_int(), ctypes.c_int()
+    c, b = ctypes.c_uint64(), ctypes.c_size_t()
+    _check(lib().gf_server_status(s, ctypes.byref(q), ctypes.byref(r), ctypes.byref(c), ctypes.byref(b)),
+           "gf_server_status")
+    return dict(queued=q.value, running=r.value, completed=c.value, bytes_in_use=b.value)
+
+
+def gf_server_destroy(s):
+    if s:
+        lib().gf_server_destroy(s)
 
 
 def gf_philox(seed, counters):
