@@ -21,6 +21,12 @@ Multi-GPU (torchrun): every rank fixes its own copies (independent
 problems, weak scaling); the only cross-rank traffic is the barrier and the
 max over ranks of the elapsed time.
 
+--serving runs the serving workload instead: a Poisson stream of jobs
+(lattices 16^4, 24^3 x 48, 32^4, 48^3 x 96; Landau, Coulomb or MAG; mixed
+precision; eps = 0.3, seed 4) through the job server, first all at once to
+measure the saturated job rate, then at a fraction of that rate; it prints
+one JSON line with p50/p99 latency and site-updates/s.
+
 --impl reference times the FP64 CPU oracle (the plain reference this
 project checks against) on the host cores, on this same workload.
 """
@@ -404,6 +410,91 @@ def run_ours(args, rank, world, local_rank):
     field.close()
 
 
+SERVING = dict(name="serving_poisson_mixed", seed=4, eps=0.3, field_seed=4, check=20, reunit=100,
+               omega={"landau": 1.7, "coulomb": 1.7, "mag": 1.35})
+
+
+def run_serving(args):
+    """Serving workload through gf_server_*: job k of the seeded stream fixes
+    the lattice's eps = 0.3 field, moved to a fresh point of its gauge orbit
+    by the job's own Haar seed, to theta < --serve-theta (FP32 -> FP64 switch
+    a decade below), at most --serve-max-sweeps sweeps; a job that reaches
+    the cap counts as finished and unconverged."""
+    import torch
+
+    from paper_1212_5221_gb300 import build, gf, inputs
+
+    build.build_all()
+    S = SERVING
+    n = args.serve_jobs
+    jobs = inputs.poisson_jobs(n, 1.0, S["seed"])  # unit-rate gaps; scaled per load below
+    fields = {}
+    for j in jobs:
+        if j["dims"] not in fields:
+            fields[j["dims"]] = inputs.links(j["dims"], "smooth", S["eps"], S["field_seed"])
+    foot = {(d, g): gf.gf_footprint(d, 1, g, "mixed") for d in fields for g in ("landau", "coulomb", "mag")}
+    free, _ = torch.cuda.mem_get_info()
+    arena = int(min(0.6 * free, args.serve_slots * max(foot.values()) * 1.1))
+    log(f"serving: {n} jobs, {args.serve_slots} slots, arena {arena / 1e9:.1f} GB")
+
+    def run(rate):
+        srv = gf.gf_server_create(arena, args.serve_slots)
+        results, t0 = [], time.time()
+        try:
+            for k, j in enumerate(jobs):
+                if rate:
+                    wait = j["arrival"] / rate - (time.time() - t0)
+                    if wait > 0:
+                        results += gf.gf_server_poll(srv, 256, int(wait * 1e3))
+                        while time.time() - t0 < j["arrival"] / rate:
+                            results += gf.gf_server_poll(srv, 256, 1)
+                th = args.serve_theta
+                gf.gf_server_submit(srv, j["dims"], j["gauge"], "mixed", host_links=fields[j["dims"]],
+                                    orbit_seed=j["seed"], tag=k, param=S["omega"][j["gauge"]], theta_target=th,
+                                    max_sweeps=args.serve_max_sweeps, check_interval=S["check"],
+                                    reunit_interval=S["reunit"], switch_theta=th / 10)
+            while len(results) < n:
+                results += gf.gf_server_poll(srv, 256, 1000)
+        finally:
+            gf.gf_server_destroy(srv)
+        bad = [r for r in results if r["status"] not in (0, gf.GF_ENOTCONV)]
+        if bad:
+            raise RuntimeError(f"{len(bad)} jobs failed, first status {bad[0]['status']}")
+        t_first = min(r["t_submit"] for r in results)
+        span = max(r["t_done"] for r in results) - t_first
+        lat = np.array([r["t_done"] - r["t_submit"] for r in results])
+        su = float(sum(r["site_updates"] for r in results))
+        return dict(jobs=n, seconds=span, jobs_per_s=n / span, site_updates_per_s=su / span,
+                    p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
+                    mean_s=float(lat.mean()), max_s=float(lat.max()),
+                    queue_p50_s=float(np.percentile([r["t_admit"] - r["t_submit"] for r in results], 50)),
+                    unconverged=sum(r["status"] == gf.GF_ENOTCONV for r in results),
+                    fp64_sweeps=sum(r["sweeps_fp64"] for r in results),
+                    sweeps=sum(r["sweeps"] for r in results))
+
+    with Clocks(0) as clocks:
+        sat = run(0.0)
+        log("saturated:", json.dumps(sat))
+        loads = []
+        for f in args.serve_loads:
+            rate = f * sat["jobs_per_s"]
+            r = run(rate)
+            r.update(load=f, rate_jobs_per_s=rate)
+            loads.append(r)
+            log("poisson:", json.dumps(r))
+    head = loads[0] if loads else sat
+    line = {"metric": "job p50/p99 latency (serving)", "value": head["p99_s"], "unit": "s (p99)", "n_gpus": 1,
+            "steps": n, "warmup": 0, "ms_per_step": head["seconds"] / n * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": S["name"], "jobs": n, "stream_seed": S["seed"],
+                       "lattices": ["16^4", "24^3x48", "32^4", "48^3x96"], "gauges": ["landau", "coulomb", "mag"],
+                       "precision": "mixed", "theta_target": args.serve_theta,
+                       "max_sweeps": args.serve_max_sweeps, "slots": args.serve_slots, "arena_bytes": arena},
+            "p50_s": head["p50_s"], "p99_s": head["p99_s"], "site_updates_per_s": head["site_updates_per_s"],
+            "saturated": sat, "poisson": loads, "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_kernel_target(args):
     """Short, fixed launch sequences on the workload's lattice for ncu captures.
     fp32 / fp64 / mixed: 3 sweeps in that precision (mixed: FP32 sweeps that
@@ -449,9 +540,19 @@ def main():
     ap.add_argument("--no-fp64-baseline", dest="fp64_baseline", action="store_false")
     ap.add_argument("--kernel-target", choices=["fp32", "fp64", "mixed", "window"], default=None,
                     help="only run a short, fixed launch sequence of the workload (for ncu)")
+    ap.add_argument("--serving", action="store_true", help="run the serving workload (job p50/p99)")
+    ap.add_argument("--serve-jobs", type=int, default=2000)
+    ap.add_argument("--serve-theta", type=float, default=1e-10)
+    ap.add_argument("--serve-max-sweeps", type=int, default=5000)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-loads", type=lambda v: [float(x) for x in v.split(",") if x], default=[0.7],
+                    help="Poisson rates as fractions of the measured saturated job rate")
     args = ap.parse_args()
     if args.kernel_target:
         run_kernel_target(args)
+        return
+    if args.serving:
+        run_serving(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
