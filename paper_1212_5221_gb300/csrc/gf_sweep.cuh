@@ -398,19 +398,323 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Landau and Coulomb gauge: the same half-sweep in K form.  Because every
+// subgroup step left-multiplies all of a site's slots by the same g, the
+// gathered K (Eq. Kx) obeys K <- g K, and the slots need the product
+// G = g2 g1 g0 only once (Step 2 of Alg. 1 applied after the three Step-1
+// subgroup choices; identical in exact arithmetic to updating the links
+// subgroup by subgroup).  The three quaternions are taken from K, of which
+// only the entries that a later subgroup reads are kept current.  Up-links
+// become G U (rows 0,1, which read all three rows of U), down-links D G^dag
+// (rows 0,1 of D only).  FP64 with eight links per lane reads the links
+// again for the update (from L2) instead of holding all eight in registers.
+template <typename R>
+struct su2m {  // [[h00 h01] [h10 h11]] of a unit quaternion (Cayley-Klein form)
+  cx<R> h00, h01, h10, h11;
+};
+template <typename R>
+__device__ __forceinline__ su2m<R> su2_of(const quat<R>& g) {
+  return {{g.q0, g.q3}, {g.q2, g.q1}, {-g.q2, g.q1}, {g.q0, -g.q3}};
+}
+
+// Step 1 for subgroup (i, j) of the current K entries: the maximiser of
+// Re tr(g W) and the update rule of the algorithm.
+template <typename R, int ALGO>
+__device__ __forceinline__ quat<R> choose_k(cx<R> W00, cx<R> W01, cx<R> W10, cx<R> W11, R param, const Rng& rng,
+                                            uint32_t sub) {
+  const quat<R> m{W00.re + W11.re, -(W01.im + W10.im), -(W01.re - W10.re), -(W00.im - W11.im)};
+  if (ALGO == ALG_OR) return rule_or(m, param);
+  if (ALGO == ALG_MICRO) return rule_micro(m);
+  if (ALGO == ALG_SR) {
+    double ua, ub;
+    rng.draw2(TAG_SR, sub, 0, ua, ub);
+    return ((R)ua < param) ? rule_micro(m) : rule_or(m, R(1));
+  }
+  return rule_sa_landau(m, param, rng, sub);
+}
+
+// FP64 contribution of a slot to K, from its stored rows (row 2 rebuilt in
+// FP64: what a later read of the links gives).
+template <typename R>
+__device__ __forceinline__ void add_stored_fp64(const mat3<R>& rows, bool down, double (&kr)[3][3],
+                                                double (&ki)[3][3]) {
+  mat3<double> d;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) d.e[a][b] = {(double)rows.e[a][b].re, (double)rows.e[a][b].im};
+  reconstruct_row2(d);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      kr[a][b] += down ? d.e[b][a].re : d.e[a][b].re;
+      ki[a][b] += down ? -d.e[b][a].im : d.e[a][b].im;
+    }
+}
+
+// theta_site = tr[Delta Delta^dag], Delta = traceless part of (K - K^dag)/(2i).
+__device__ __forceinline__ double theta_of_k(const double (&kr)[3][3], const double (&ki)[3][3]) {
+  double dr[3][3], di[3][3], th = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      dr[a][b] = 0.5 * (ki[a][b] + ki[b][a]);
+      di[a][b] = -0.5 * (kr[a][b] - kr[b][a]);
+    }
+  const double tr3 = (dr[0][0] + dr[1][1] + dr[2][2]) / 3.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) dr[a][a] -= tr3;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) th += dr[a][b] * dr[a][b] + di[a][b] * di[a][b];
+  return th;
+}
+
+template <int L>
+__device__ __forceinline__ void butterfly_k(double (&kr)[3][3], double (&ki)[3][3]) {
+#pragma unroll
+  for (int o = 1; o < L; o <<= 1)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        kr[a][b] += __shfl_xor_sync(FULL, kr[a][b], o);
+        ki[a][b] += __shfl_xor_sync(FULL, ki[a][b], o);
+      }
+}
+
+// rows 0,1 of G t (t with all three rows)
+template <typename R>
+__device__ __forceinline__ void apply_left(const mat3<R>& G, const mat3<R>& t, mat3<R>& n) {
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const cx<R> x = cmul2(G.e[r][0], t.e[0][c], G.e[r][1], t.e[1][c]);
+      n.e[r][c] = {x.re + G.e[r][2].re * t.e[2][c].re - G.e[r][2].im * t.e[2][c].im,
+                   x.im + G.e[r][2].re * t.e[2][c].im + G.e[r][2].im * t.e[2][c].re};
+    }
+}
+// rows 0,1 of t G^dag (t's rows 0,1 only)
+template <typename R>
+__device__ __forceinline__ void apply_right_dag(const mat3<R>& G, const mat3<R>& t, mat3<R>& n) {
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const cx<R> x = cmul2c(t.e[r][0], G.e[c][0], t.e[r][1], G.e[c][1]);
+      n.e[r][c] = {x.re + t.e[r][2].re * G.e[c][2].re + t.e[r][2].im * G.e[c][2].im,
+                   x.im + t.e[r][2].im * G.e[c][2].re - t.e[r][2].re * G.e[c][2].im};
+    }
+}
+
+template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
+__device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t copy, uint32_t sp, bool valid,
+                                             int lane) {
+  constexpr int NC = store_traits<R>::NC;
+  constexpr int L = 8 / LPT;
+  constexpr bool KEEP = sizeof(R) == 4 || LPT <= 4;
+  const Geom& Gm = a.geom;
+  const uint32_t Vh = Gm.Vh;
+  int c[4] = {0, 0, 0, 0};
+  uint32_t s = 0;
+  if (valid) {
+    site_coords(Gm, sp, a.parity, c, s);
+    if (a.active && !a.active[(size_t)copy * Gm.n[0] + c[0]]) valid = false;
+  }
+  // rows re-projected at load: every FP32 kernel, and the FP64 kernels whose
+  // rotations stay large (heat bath, microcanonical, SR); a read-only pass
+  // leaves them as stored
+  const bool NORM = (sizeof(R) == 4 || ALGO != ALG_OR) && (!OBS || a.update);
+
+  size_t off[LPT];
+  bool use[LPT], gather[LPT], dn[LPT];
+#pragma unroll
+  for (int j = 0; j < LPT; ++j) {
+    const int k = lane * LPT + j;
+    const int mu = k >> 1;
+    const bool down = (LPT >= 2) ? (j & 1) : (k & 1);
+    dn[j] = down;
+    gather[j] = !(GAUGE == COULOMB && mu == 0);
+    use[j] = valid && !(GAUGE == COULOMB && mu == 0 && down);
+    const int slot = (GAUGE == COULOMB && mu == 0) ? 4 : mu;
+    uint32_t ssp = sp;
+    int par = a.parity;
+    if (down) {
+      const int cm = mu == 0 ? c[0] : mu == 1 ? c[1] : mu == 2 ? c[2] : c[3];
+      const int nm = mu == 0 ? Gm.n[0] : mu == 1 ? Gm.n[1] : mu == 2 ? Gm.n[2] : Gm.n[3];
+      const uint32_t st = mu == 0 ? Gm.stride[0] : mu == 1 ? Gm.stride[1] : mu == 2 ? Gm.stride[2] : 1u;
+      ssp = (cm > 0 ? s - st : s + (uint32_t)(nm - 1) * st) >> 1;
+      par ^= 1;
+    }
+    off[j] = link_off(copy, par, slot, a.NS, NC, Vh, ssp);
+  }
+
+  // gather: K = sum of U_mu(x) and U_mu(x - mu)^dag over the lane's slots
+  mat3<R> u[KEEP ? LPT : 1];
+  mat3<R> K;
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+#pragma unroll
+    for (int y = 0; y < 3; ++y) K.e[x][y] = {R(0), R(0)};
+  constexpr bool OBS_FP64 = OBS && sizeof(R) == 4;  // FP32 kernels gather the FP64 K separately
+  double kr[3][3], ki[3][3];
+  if (OBS) {
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+#pragma unroll
+      for (int y = 0; y < 3; ++y) kr[x][y] = ki[x][y] = 0.0;
+  }
+#pragma unroll
+  for (int j = 0; j < LPT; ++j) {
+    mat3<R> t;
+    if (use[j]) {
+      load_rows(a.links + off[j], Vh, t);
+      if (NORM) reproject_rows(t);
+    } else {
+      set_identity(t);
+    }
+    if (KEEP) u[KEEP ? j : 0] = t;
+    if (use[j] && gather[j]) {
+      if (OBS_FP64 && a.obs == 1) add_stored_fp64(t, dn[j], kr, ki);
+      reconstruct_row2(t);
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) {
+          const cx<R> v = dn[j] ? cx<R>{t.e[y][x].re, -t.e[y][x].im} : t.e[x][y];
+          K.e[x][y].re += v.re;
+          K.e[x][y].im += v.im;
+        }
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < L; o <<= 1)
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+#pragma unroll
+      for (int y = 0; y < 3; ++y) {
+        K.e[x][y].re += __shfl_xor_sync(FULL, K.e[x][y].re, o);
+        K.e[x][y].im += __shfl_xor_sync(FULL, K.e[x][y].im, o);
+      }
+
+  if (OBS && a.obs == 1) {  // theta of the current links at this site (K as gathered)
+    if (OBS_FP64) {
+      butterfly_k<L>(kr, ki);
+    } else {
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) {
+          kr[x][y] = (double)K.e[x][y].re;
+          ki[x][y] = (double)K.e[x][y].im;
+        }
+    }
+    if (valid && lane == 0) a.obs_site[(size_t)copy * Gm.V + s] = make_double2(0.0, theta_of_k(kr, ki));
+  }
+  if (OBS && !a.update) return;
+
+  // Step 1: the three subgroups in the order (0,1), (0,2), (1,2)
+  Rng rng{a.k0, a.k1, s, a.sweep, a.copy0 + copy};
+  const su2m<R> h0 = su2_of(choose_k<R, ALGO>(K.e[0][0], K.e[0][1], K.e[1][0], K.e[1][1], a.param, rng, 0u));
+  {  // K <- g0 K on the entries read later: row 0, and row 1 columns 1, 2
+    cx<R> r0[3];
+#pragma unroll
+    for (int y = 0; y < 3; ++y) r0[y] = cmul2(h0.h00, K.e[0][y], h0.h01, K.e[1][y]);
+#pragma unroll
+    for (int y = 1; y < 3; ++y) K.e[1][y] = cmul2(h0.h10, K.e[0][y], h0.h11, K.e[1][y]);
+#pragma unroll
+    for (int y = 0; y < 3; ++y) K.e[0][y] = r0[y];
+  }
+  const su2m<R> h1 = su2_of(choose_k<R, ALGO>(K.e[0][0], K.e[0][2], K.e[2][0], K.e[2][2], a.param, rng, 1u));
+#pragma unroll
+  for (int y = 1; y < 3; ++y) K.e[2][y] = cmul2(h1.h10, K.e[0][y], h1.h11, K.e[2][y]);  // row 2 of g1 K
+  const su2m<R> h2 = su2_of(choose_k<R, ALGO>(K.e[1][1], K.e[1][2], K.e[2][1], K.e[2][2], a.param, rng, 2u));
+
+  // G = g2 g1 g0 in the 3x3 embedding
+  mat3<R> G;
+  {
+    // g1 g0: rows 0 and 2 mixed, row 1 = row 1 of g0
+    const cx<R> r00 = cmul(h1.h00, h0.h00), r01 = cmul(h1.h00, h0.h01);
+    const cx<R> r20 = cmul(h1.h10, h0.h00), r21 = cmul(h1.h10, h0.h01);
+    G.e[0][0] = r00;
+    G.e[0][1] = r01;
+    G.e[0][2] = h1.h01;
+    // g2 on rows 1 = (h0.h10, h0.h11, 0) and 2 = (r20, r21, h1.h11)
+    G.e[1][0] = cmul2(h2.h00, h0.h10, h2.h01, r20);
+    G.e[1][1] = cmul2(h2.h00, h0.h11, h2.h01, r21);
+    G.e[1][2] = cmul(h2.h01, h1.h11);
+    G.e[2][0] = cmul2(h2.h10, h0.h10, h2.h11, r20);
+    G.e[2][1] = cmul2(h2.h10, h0.h11, h2.h11, r21);
+    G.e[2][2] = cmul(h2.h11, h1.h11);
+  }
+
+  // mixed precision: the site's accumulated gauge transformation (FP32 working copy only)
+  constexpr bool CAN_ACC = sizeof(R) == 4 && GAUGE != COULOMB;
+  if (CAN_ACC && a.acc && valid && lane == 0) {
+    const size_t acc_off = link_off(copy, a.parity, 4, a.NS, NC, Vh, sp);
+    mat3<R> t, n;
+    load_rows(a.links + acc_off, Vh, t);
+    reproject_rows(t);
+    reconstruct_row2(t);
+    apply_left(G, t, n);
+    store_rows(a.links + acc_off, Vh, n);
+  }
+
+  // Step 2: apply G to the slots; fused F and theta of the written links
+  double F = 0.0;
+  if (OBS && a.obs == 2) {
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+#pragma unroll
+      for (int y = 0; y < 3; ++y) kr[x][y] = ki[x][y] = 0.0;
+  }
+#pragma unroll
+  for (int j = 0; j < LPT; ++j) {
+    if (!use[j]) continue;
+    mat3<R> t, n;
+    if (KEEP) {
+      t = u[KEEP ? j : 0];
+    } else {
+      load_rows(a.links + off[j], Vh, t);
+      if (NORM) reproject_rows(t);
+    }
+    if (dn[j]) {
+      apply_right_dag(G, t, n);
+    } else {
+      reconstruct_row2(t);
+      apply_left(G, t, n);
+    }
+    store_rows(a.links + off[j], Vh, n);
+    if (OBS && a.obs == 2 && gather[j]) add_stored_fp64(n, dn[j], kr, ki);
+  }
+  if (OBS && a.obs == 2) {
+    butterfly_k<L>(kr, ki);
+    F = kr[0][0] + kr[1][1] + kr[2][2];
+    if (valid && lane == 0) a.obs_site[(size_t)copy * Gm.V + s] = make_double2(F, theta_of_k(kr, ki));
+  }
+}
+
 // Resident blocks per SM requested from the register allocator: FP32 keeps
-// 2-4 blocks of 256 threads per SM (<= 128 / 85 / 64 registers); FP64 with
-// eight or four links per thread needs the whole register file.
-template <typename R, int LPT>
+// 2-4 blocks of 256 threads per SM (<= 128 / 85 / 64 registers).  FP64 in K
+// form fits two blocks with eight links per lane (the links are read again
+// for the update) and one with four or two (links held in registers); the
+// per-slot MAG form needs the whole register file for four or eight.
+template <typename R, int GAUGE, int LPT>
 constexpr int min_blocks() {
   return sizeof(R) == 4 ? (LPT == 8 ? 1 : LPT == 4 ? 2 : LPT == 2 ? 3 : 4)
-                        : (LPT >= 4 ? 1 : LPT == 2 ? 2 : 3);
+         : GAUGE == MAG ? (LPT >= 4 ? 1 : LPT == 2 ? 2 : 3)
+                        : (LPT == 8 ? 2 : LPT >= 2 ? 1 : 2);
 }
 
 // OBS: the variant with the fused observables (used for overrelaxation check
 // sweeps only, so that the plain kernels keep their register budget).
 template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
-__global__ void __launch_bounds__(BLOCK, min_blocks<R, LPT>()) sweep_kernel(const SweepArgs<R> a) {
+__global__ void __launch_bounds__(BLOCK, min_blocks<R, GAUGE, LPT>()) sweep_kernel(const SweepArgs<R> a) {
   constexpr int NC = store_traits<R>::NC;
   constexpr int L = 8 / LPT;
   constexpr uint32_t TILE = BLOCK / L;
@@ -428,7 +732,10 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R, LPT>()) sweep_kernel(cons
     }
     const uint32_t copy = (uint32_t)(tile / tiles_per_copy);
     const uint32_t sp = (uint32_t)(tile - (uint64_t)copy * tiles_per_copy) * TILE + local;
-    sweep_site<R, GAUGE, ALGO, LPT, OBS>(a, copy, sp, sp < Vh, lane);
+    if constexpr (GAUGE == MAG)
+      sweep_site<R, GAUGE, ALGO, LPT, OBS>(a, copy, sp, sp < Vh, lane);
+    else
+      sweep_site_k<R, GAUGE, ALGO, LPT, OBS>(a, copy, sp, sp < Vh, lane);
   }
 }
 
