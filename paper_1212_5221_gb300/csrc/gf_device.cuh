@@ -203,6 +203,9 @@ struct Rng {
 // Math wrappers per precision.
 __device__ __forceinline__ float rsqrt_(float x) { return 1.0f / sqrtf(x); }
 __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
+// the math library's reciprocal square root (a few ulp, no division)
+__device__ __forceinline__ float rsq_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq_(double x) { return rsqrt(x); }
 __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 __device__ __forceinline__ float log_(float x) { return logf(x); }
@@ -246,13 +249,18 @@ __device__ __forceinline__ quat<R> qidentity() {
 // g = (c a0, b c a).  w = 1 is relaxation.  A zero m gives the identity.
 template <typename R>
 __device__ __forceinline__ quat<R> rule_or(quat<R> m, R omega) {
+  // on the normalised quaternion (a0^2 + |a|^2 = 1), so that two reciprocal
+  // square roots replace the division and the square root
   R a0 = m.q0 * m.q0;
   R ai = m.q1 * m.q1 + m.q2 * m.q2 + m.q3 * m.q3;
   R den = a0 + ai;
   if (den == R(0)) return qidentity<R>();
-  R b = (omega * a0 + ai) / den;
-  R c = rsqrt_(a0 + b * b * ai);
-  R bc = b * c;
+  const R s = rsq_(den);
+  const R s2 = s * s;
+  const R x0 = a0 * s2, xi = ai * s2;
+  const R b = omega * x0 + xi;
+  const R c = rsq_(x0 + b * b * xi) * s;
+  const R bc = b * c;
   return {c * m.q0, bc * m.q1, bc * m.q2, bc * m.q3};
 }
 
@@ -261,7 +269,7 @@ template <typename R>
 __device__ __forceinline__ quat<R> rule_micro(quat<R> m) {
   R n2 = m.q0 * m.q0 + m.q1 * m.q1 + m.q2 * m.q2 + m.q3 * m.q3;
   if (n2 == R(0)) return qidentity<R>();
-  R inv = R(1) / sqrt_(n2);
+  R inv = rsq_(n2);
   R h0 = m.q0 * inv;
   R f = R(2) * h0 * inv;
   return {R(2) * h0 * h0 - R(1), f * m.q1, f * m.q2, f * m.q3};
