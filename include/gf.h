@@ -179,11 +179,20 @@ int gf_set_copy_base(gf_ctx* ctx, uint32_t base);
  * keeps the fastest for each (precision, algorithm) it is asked about. */
 int gf_set_links_per_thread(gf_ctx* ctx, int lpt);
 
-/* The sweep kernels run a persistent grid over tiles of sites and, when on
- * (the default), prefetch each block's next tile of links into L2 with
- * bulk prefetches while the current tile is processed.  Results do not
- * depend on this switch. */
-int gf_set_prefetch(gf_ctx* ctx, int on);
+/* The sweep kernels run a persistent grid over tiles of sites; while a block
+ * processes one tile, its next tile is fetched:
+ *   GF_PREFETCH_NONE  not at all;
+ *   GF_PREFETCH_L2    into L2 by bulk prefetches (the default);
+ *   GF_PREFETCH_SMEM  FP32 storage: into one of two shared-memory buffers by
+ *                     bulk asynchronous copies completing on an mbarrier, from
+ *                     which the tile is then processed (FP64 storage falls
+ *                     back to GF_PREFETCH_L2).  A wait for a buffer is bounded
+ *                     (about 2 s); if one runs out, the kernel stops, records
+ *                     it, and the next call that reads results back returns
+ *                     GF_ETIMEOUT.
+ * Results do not depend on the mode.  GF_EINVAL for any other value. */
+enum { GF_PREFETCH_NONE = 0, GF_PREFETCH_L2 = 1, GF_PREFETCH_SMEM = 2 };
+int gf_set_prefetch(gf_ctx* ctx, int mode);
 
 /* F and theta fused into the sweeps (on by default): the odd half of the last
  * overrelaxation/relaxation sweep -- in which every link is written exactly
@@ -195,6 +204,10 @@ int gf_set_prefetch(gf_ctx* ctx, int on);
  * standalone observables pass (same values up to summation order). */
 int gf_set_fused_observables(gf_ctx* ctx, int on);
 int gf_get_links_per_thread(gf_ctx* ctx, int* lpt);
+/* Time each links-per-thread choice (and, for FP32 storage, both the L2
+ * prefetch and the shared-memory staging of tiles) on a scratch copy of the
+ * links, restore them, and keep the fastest for (storage precision, algo).
+ * A later gf_set_prefetch replaces the tuned tile fetch. */
 int gf_autotune(gf_ctx* ctx, gf_algo algo, int* best_lpt, double* ms_per_sweep_best);
 
 /* Drive the sweeps to theta < theta_target (the while-loop of Alg. 1).

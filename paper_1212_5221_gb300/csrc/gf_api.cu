@@ -44,8 +44,8 @@ constexpr size_t STAGING_BYTES = (size_t)256 << 20;
 size_t round_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t links32 = 0, links64 = 0, gscratch = 0, obs_site = 0, active = 0, partial = 0, obs = 0, staging = 0,
-         total = 0;
+  size_t links32 = 0, links64 = 0, gscratch = 0, obs_site = 0, active = 0, partial = 0, obs = 0, err = 0,
+         staging = 0, total = 0;
   int slab_nt = 1;
 };
 
@@ -97,10 +97,11 @@ Layout make_layout(const int dims[4], int ncopies, int gauge, int prec) {
   L.active = round_up((size_t)ncopies * dims[0] * sizeof(int));
   L.partial = round_up(gfk::observables_partial_doubles(G, ncopies) * sizeof(double));
   L.obs = round_up((size_t)ncopies * dims[0] * 2 * sizeof(double));
+  L.err = ALIGN;  // the sweep kernels' error word
   const size_t slice_bytes = (size_t)G.V3 * 4 * 18 * sizeof(double);
   L.slab_nt = (int)std::max<size_t>(1, std::min<size_t>(dims[0], STAGING_BYTES / slice_bytes));
   L.staging = round_up((size_t)L.slab_nt * slice_bytes);
-  L.total = L.links32 + L.links64 + L.gscratch + L.obs_site + L.active + L.partial + L.obs + L.staging;
+  L.total = L.links32 + L.links64 + L.gscratch + L.obs_site + L.active + L.partial + L.obs + L.err + L.staging;
   return L;
 }
 
@@ -124,6 +125,8 @@ struct gf_ctx {
   int* active_d = nullptr;
   double* partial = nullptr;
   double* obs_d = nullptr;
+  int* err_d = nullptr;      // set by a sweep kernel whose staging wait ran out
+  bool err_pending = false;  // a staged sweep ran since err_d was last read
   double* staging = nullptr;
   bool fp64 = false;   // storage the sweeps run on
   bool dirty = false;  // GF_MIXED: FP32 sweeps not yet applied to the FP64 master
@@ -131,9 +134,10 @@ struct gf_ctx {
   std::vector<int> active_h;
   uint64_t sweep_index = 0;
   uint32_t copy_base = 0;  // Philox copy id of copy 0
-  int prefetch = 1;        // L2 prefetch of the next tile in the sweep kernels
+  int prefetch = GF_PREFETCH_L2;  // how the sweep kernels fetch the next tile
   int fused_obs = 1;       // F/theta fused into the last OR sweep where possible
   int lpt[2][5] = {{0}};  // [fp64][algo] chosen links per thread, 0 = default
+  int pmode[2][5] = {{0}};  // [fp64][algo] tile fetch chosen by gf_autotune + 1, 0 = the context's
   // optional per-kernel timing: CUDA events around every launch of a class
   uint64_t launch_count = 0;  // every kernel this context launched
   bool profiling = false;
@@ -204,7 +208,8 @@ int default_lpt(const gf_ctx* c, int algo) {
 }
 
 int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, uint32_t sweep, int lpt,
-                int obs = 0, int update = 1) {
+                int obs = 0, int update = 1, int pmode = -1) {
+  const int prefetch = pmode >= 0 ? pmode : c->prefetch;
   cudaError_t e;
   if (c->fp64) {
     gfk::SweepArgs<double> a;
@@ -219,11 +224,12 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     a.k0 = (uint32_t)seed;
     a.k1 = (uint32_t)(seed >> 32);
     a.sweep = sweep;
-    a.prefetch = c->prefetch;
+    a.prefetch = prefetch;
     a.acc = (update && c->prec == GF_MIXED && !c->fp64 && c->gauge != GF_COULOMB) ? 1 : 0;
     a.obs = obs;
     a.update = update;
     a.obs_site = static_cast<double2*>(c->obs_site);
+    a.err = c->err_d;
     cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<double>(a, c->gauge, kalgo, lpt, c->st);
     prof_end(c, t0, GF_KERNEL_SWEEP_FP64);
@@ -241,11 +247,13 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     a.k0 = (uint32_t)seed;
     a.k1 = (uint32_t)(seed >> 32);
     a.sweep = sweep;
-    a.prefetch = c->prefetch;
+    a.prefetch = prefetch;
     a.acc = (update && c->prec == GF_MIXED && !c->fp64 && c->gauge != GF_COULOMB) ? 1 : 0;
     a.obs = obs;
     a.update = update;
     a.obs_site = static_cast<double2*>(c->obs_site);
+    a.err = c->err_d;
+    if (a.prefetch == GF_PREFETCH_SMEM) c->err_pending = true;
     cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<float>(a, c->gauge, kalgo, lpt, c->st);
     prof_end(c, t0, GF_KERNEL_SWEEP_FP32);
@@ -258,15 +266,31 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
 // One full sweep (even, then odd sublattice) of kernel algorithm kalgo; with
 // obs_last the odd half also writes F and theta of its sites (fused check).
 int full_sweep(gf_ctx* c, int kalgo, int api_algo, double param, uint64_t seed, int lpt_override = 0,
-               bool obs_last = false) {
+               bool obs_last = false, int pmode_override = -1) {
   const int lpt = lpt_override ? lpt_override : default_lpt(c, api_algo);
+  const int pm = pmode_override >= 0 ? pmode_override : c->pmode[c->fp64][api_algo] - 1;
   const uint32_t sw = (uint32_t)c->sweep_index;
   for (int p = 0; p < 2; ++p) {
-    int r = launch_half(c, kalgo, param, p, seed, sw, lpt, (obs_last && p == 1) ? 2 : 0);
+    int r = launch_half(c, kalgo, param, p, seed, sw, lpt, (obs_last && p == 1) ? 2 : 0, 1, pm);
     if (r) return r;
   }
   if (c->prec == GF_MIXED && !c->fp64) c->dirty = true;
   c->sweep_index++;
+  return GF_OK;
+}
+
+// A staged sweep whose shared-memory wait ran out records it in err_d; it is
+// read at the next point where the host waits for the stream anyway.
+int read_sweep_error(gf_ctx* c) {
+  if (!c->err_pending) return GF_OK;
+  int h = 0;
+  GF_CUDA(cudaMemcpyAsync(&h, c->err_d, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  c->err_pending = false;
+  if (h) {
+    GF_CUDA(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st));
+    return fail(GF_ETIMEOUT, "a shared-memory staging wait in the sweep kernel ran out");
+  }
   return GF_OK;
 }
 
@@ -284,7 +308,7 @@ int observables_on(gf_ctx* c, std::vector<double>& per_ct, bool f64) {
                           c->st));
   GF_CUDA(cudaStreamSynchronize(c->st));
   prof_collect(c);
-  return GF_OK;
+  return read_sweep_error(c);
 }
 
 // observables of the storage the sweeps run on
@@ -306,7 +330,7 @@ int fused_observables(gf_ctx* c, std::vector<double>& per_ct) {
                           c->st));
   GF_CUDA(cudaStreamSynchronize(c->st));
   prof_collect(c);
-  return GF_OK;
+  return read_sweep_error(c);
 }
 
 void copy_means(const gf_ctx* c, const std::vector<double>& ct, double* F, double* T) {
@@ -450,8 +474,10 @@ int create_impl(const int dims[4], int ncopies, int gauge, int prec, void* strea
   c->active_d = reinterpret_cast<int*>(base + off); off += L.active;
   c->partial = reinterpret_cast<double*>(base + off); off += L.partial;
   c->obs_d = reinterpret_cast<double*>(base + off); off += L.obs;
+  c->err_d = reinterpret_cast<int*>(base + off); off += L.err;
   c->staging = reinterpret_cast<double*>(base + off); off += L.staging;
   r = upload_active(c);
+  if (!r && cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st) != cudaSuccess) r = fail(GF_ECUDA, "init of the error word");
   if (!r) r = set_identity_slots(c, 0, 4);
   if (!r) {
     cudaError_t e = cudaStreamSynchronize(c->st);
@@ -557,7 +583,7 @@ int finish_public(gf_ctx* c, double* F, double* theta) {
     return GF_OK;
   }
   GF_CUDA(cudaStreamSynchronize(c->st));
-  return GF_OK;
+  return read_sweep_error(c);
 }
 
 int reunitarize(gf_ctx* c) {
@@ -845,10 +871,12 @@ int gf_set_fused_observables(gf_ctx* c, int on) {
   return GF_OK;
 }
 
-int gf_set_prefetch(gf_ctx* c, int on) {
+int gf_set_prefetch(gf_ctx* c, int mode) {
   int r = check_ctx(c);
   if (r) return r;
-  c->prefetch = on ? 1 : 0;
+  if (mode < GF_PREFETCH_NONE || mode > GF_PREFETCH_SMEM) return fail(GF_EINVAL, "bad prefetch mode %d", mode);
+  c->prefetch = mode;
+  memset(c->pmode, 0, sizeof c->pmode);  // an explicit choice replaces the tuned ones
   return GF_OK;
 }
 
@@ -886,33 +914,42 @@ int gf_autotune(gf_ctx* c, gf_algo algo, int* best_lpt, double* ms_best) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  int best = 0;
+  int best = 0, best_mode = c->prefetch;
   float best_ms = 1e30f;
   const int cands[4] = {1, 2, 4, 8};
-  for (int lpt : cands) {
-    r = full_sweep(c, kalgo, algo, param, 1, lpt);  // warm-up
-    if (r) break;
-    const int reps = 3;
-    cudaEventRecord(e0, c->st);
-    for (int k = 0; k < reps && !r; ++k) r = full_sweep(c, kalgo, algo, param, 1, lpt);
-    cudaEventRecord(e1, c->st);
-    cudaEventSynchronize(e1);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    ms /= reps;
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = lpt;
+  // FP32 storage: both tile fetches (L2 prefetch, shared-memory staging)
+  const int modes[2] = {GF_PREFETCH_L2, GF_PREFETCH_SMEM};
+  const int nmodes = c->fp64 ? 1 : 2;
+  for (int m = 0; m < nmodes && !r; ++m) {
+    const int mode = c->fp64 ? c->prefetch : modes[m];
+    for (int lpt : cands) {
+      r = full_sweep(c, kalgo, algo, param, 1, lpt, false, mode);  // warm-up
+      if (r) break;
+      const int reps = 3;
+      cudaEventRecord(e0, c->st);
+      for (int k = 0; k < reps && !r; ++k) r = full_sweep(c, kalgo, algo, param, 1, lpt, false, mode);
+      cudaEventRecord(e1, c->st);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+      if (!r && ms < best_ms) {
+        best_ms = ms;
+        best = lpt;
+        best_mode = mode;
+      }
+      cudaMemcpyAsync(c->links(), backup, bytes, cudaMemcpyDeviceToDevice, c->st);
     }
-    cudaMemcpyAsync(c->links(), backup, bytes, cudaMemcpyDeviceToDevice, c->st);
   }
   cudaStreamSynchronize(c->st);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(backup);
   c->sweep_index = idx0;
+  if (!r) r = read_sweep_error(c);
   if (r) return r;
   c->lpt[c->fp64][algo] = best;
+  c->pmode[c->fp64][algo] = best_mode + 1;
   if (best_lpt) *best_lpt = best;
   if (ms_best) *ms_best = best_ms;
   return GF_OK;

@@ -27,6 +27,7 @@ struct SweepArgs {
                       //    update); 2 F and theta of the updated links (odd half-sweep)
   int update;         // 0: read-only pass (with obs = 1): gather, no update, no store
   double2* obs_site;  // [copy][site] (F, theta) contributions written by lane 0
+  int* err;           // set to 1 if a shared-memory staging wait ran out (prefetch 2)
 };
 
 // Per-site FP64 observables from the slot matrices M (M = U_mu(x) for up
@@ -223,6 +224,161 @@ __device__ __forceinline__ void prefetch_tile(const SweepArgs<R>& a, uint32_t co
 }
 
 // ---------------------------------------------------------------------------
+// Shared-memory staging of a tile (FP32 storage, prefetch mode 2).  While a
+// block processes one tile from one of two stage buffers, its next tile's
+// links are copied into the other by bulk asynchronous copies
+// (cp.async.bulk, completion counted in bytes on an mbarrier per buffer).
+// Region (k, chunk) of a buffer holds chunk `chunk` of slot k (k = 2 mu + d
+// for the links, k = 8 for the mixed-precision accumulator) for the parity
+// indices [lo_k, lo_k + extent_k): the tile's own range for up-links and the
+// accumulator, the range of prefetch_tile for down-links.  Indices outside
+// [0, Vh) are not copied; a site whose neighbour index lies outside the
+// copied range (periodic wrap) reads global memory instead.  Each link a
+// tile's sites read is written only by those sites (one active endpoint per
+// link in a half-sweep), so staged values are never stale.
+template <int TILE>
+struct StageGeom {
+  static constexpr int RS = TILE + 3;  // TILE + 2 rounded up to odd: link regions of the two lanes of a
+                                       // site fall 16 banks apart
+  static constexpr int ACC0 = 24 * RS;
+  static constexpr int VEC = 24 * RS + 3 * TILE;  // float4 per buffer
+  static constexpr size_t BYTES = (size_t)VEC * 16;
+  __device__ static int base(int k, int chunk) { return k < 8 ? (k * 3 + chunk) * RS : ACC0 + chunk * TILE; }
+  __device__ static int stride(int k) { return k < 8 ? RS : TILE; }
+};
+
+// Dynamic shared memory of the staged sweep: two buffers and two mbarriers.
+template <int LPT>
+constexpr size_t stage_smem_bytes() {
+  return 2 * StageGeom<BLOCK / (8 / LPT)>::BYTES + 16;
+}
+
+__device__ __forceinline__ void stage_range(const Geom& G, uint32_t sp0, uint32_t tile, int k, int64_t& lo,
+                                            uint32_t& clo, uint32_t& chi) {
+  int64_t ext = tile;
+  lo = sp0;
+  if (k < 8 && (k & 1)) {
+    const int mu = k >> 1;
+    const uint32_t st = mu == 0 ? G.stride[0] : mu == 1 ? G.stride[1] : mu == 2 ? G.stride[2] : 0u;
+    lo = (int64_t)sp0 - (int64_t)(st / 2) - 1;
+    ext = (int64_t)tile + 2;
+  }
+  // clipped to [0, Vh) in signed arithmetic: a down-link range near the start
+  // of the lattice can end below zero (empty then)
+  int64_t c0 = lo < 0 ? 0 : lo, c1 = lo + ext;
+  if (c1 > (int64_t)G.Vh) c1 = G.Vh;
+  if (c0 > (int64_t)G.Vh) c0 = G.Vh;
+  if (c1 < c0) c1 = c0;
+  clo = (uint32_t)c0;
+  chi = (uint32_t)c1;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t tx) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase with the given parity to complete, for at most about
+// two seconds (and 2^24 polls); false if it did not.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t i = 0; i < (1u << 24); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 63u && globaltimer_ns() - t0 > 2000000000ull) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Warp 0 of the block: copy the tile at (copy, sp0) into buffer buf and arm
+// its mbarrier with the byte count.  Lane r < 24 copies region (r / 3, r % 3),
+// lanes 24..26 the accumulator's chunks when the accumulator is in use.
+template <int GAUGE, int TILE>
+__device__ __forceinline__ void stage_issue(const SweepArgs<float>& a, uint32_t copy, uint32_t sp0, float4* buf,
+                                            uint32_t bar, int lane) {
+  using SG = StageGeom<TILE>;
+  uint32_t bytes = 0, dst = 0;
+  const float4* src = nullptr;
+  const bool acc = GAUGE != COULOMB && a.acc;
+  if (lane < 24 || (acc && lane < 27)) {
+    const int k = lane < 24 ? lane / 3 : 8;
+    const int chunk = lane < 24 ? lane % 3 : lane - 24;
+    if (!(GAUGE == COULOMB && k == 1)) {  // Coulomb: U_0(x - 0) is not touched
+      int64_t lo;
+      uint32_t clo, chi;
+      stage_range(a.geom, sp0, TILE, k, lo, clo, chi);
+      if (chi > clo) {
+        const int mu = k >> 1;
+        const bool down = k < 8 && (k & 1);
+        const int par = down ? a.parity ^ 1 : a.parity;
+        const int slot = k == 8 ? 4 : (GAUGE == COULOMB && mu == 0) ? 4 : mu;
+        src = a.links + link_off(copy, par, slot, a.NS, 3, a.geom.Vh, 0) + (size_t)chunk * a.geom.Vh + clo;
+        dst = smem_u32(buf + SG::base(k, chunk) + (int)(clo - lo));
+        bytes = (chi - clo) * 16u;
+      }
+    }
+  }
+  const uint32_t total = __reduce_add_sync(FULL, bytes);
+  if (lane == 0) mbar_arrive_expect_tx(bar, total);
+  __syncwarp();
+  if (bytes) bulk_g2s(dst, src, bytes, bar);
+}
+
+// Rows 0,1 of slot k's link at parity index idx: from the stage buffer when
+// it holds that index, else from global memory.
+template <typename R, int TILE>
+__device__ __forceinline__ void load_slot(const float4* stage, const Geom& G, uint32_t sp0, int k, uint32_t idx,
+                                          const typename store_traits<R>::vec* g, uint32_t Vh, mat3<R>& u) {
+  if constexpr (sizeof(R) == 4) {
+    if (stage) {
+      int64_t lo;
+      uint32_t clo, chi;
+      stage_range(G, sp0, TILE, k, lo, clo, chi);
+      if (idx >= clo && idx < chi) {
+        using SG = StageGeom<TILE>;
+        const float4* p = stage + SG::base(k, 0) + (int)(idx - lo);
+        const int rs = SG::stride(k);
+        const float4 x = p[0], y = p[rs], z = p[2 * rs];
+        u.e[0][0] = {x.x, x.y};
+        u.e[0][1] = {x.z, x.w};
+        u.e[0][2] = {y.x, y.y};
+        u.e[1][0] = {y.z, y.w};
+        u.e[1][1] = {z.x, z.y};
+        u.e[1][2] = {z.z, z.w};
+        return;
+      }
+    }
+  }
+  load_rows(g, Vh, u);
+}
+
+// ---------------------------------------------------------------------------
 // One half-sweep (Alg. 1 for one sublattice).  L = 8/LPT lanes share a site;
 // lane l holds slots l*LPT .. l*LPT+LPT-1 of the site's eight links, slot
 // k = 2 mu + d: d = 0 is U_mu(x), d = 1 is U_mu(x - mu)^dagger, so that every
@@ -237,7 +393,8 @@ __device__ __forceinline__ void prefetch_tile(const SweepArgs<R>& a, uint32_t co
 // its next tile into L2 while it works on the current one.
 template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
 __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy, uint32_t sp, bool valid,
-                                           int lane) {
+                                           int lane, const float4* stage, uint32_t sp0) {
+  constexpr uint32_t TILE = BLOCK / (8 / LPT);
   constexpr int NC = store_traits<R>::NC;
   constexpr int L = 8 / LPT;
   const Geom& G = a.geom;
@@ -277,7 +434,7 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
     }
     off[j] = link_off(copy, par, slot, a.NS, NC, Vh, ssp);
     if (use[j]) {
-      load_rows(a.links + off[j], Vh, u[j]);
+      load_slot<R, TILE>(stage, G, sp0, k, ssp, a.links + off[j], Vh, u[j]);
       if (NORM) reproject_rows(u[j]);
       reconstruct_row2(u[j]);
       if (down) dagger(u[j]);
@@ -296,7 +453,7 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
   if (acc) {
     if (use_acc) {
       acc_off = link_off(copy, a.parity, 4, a.NS, NC, Vh, sp);
-      load_rows(a.links + acc_off, Vh, gacc);
+      load_slot<R, TILE>(stage, G, sp0, 8, sp, a.links + acc_off, Vh, gacc);
       reproject_rows(gacc);
       reconstruct_row2(gacc);
     } else {
@@ -514,7 +671,8 @@ __device__ __forceinline__ void apply_right_dag(const mat3<R>& G, const mat3<R>&
 
 template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
 __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t copy, uint32_t sp, bool valid,
-                                             int lane) {
+                                             int lane, const float4* stage, uint32_t sp0) {
+  constexpr uint32_t TILE = BLOCK / (8 / LPT);
   constexpr int NC = store_traits<R>::NC;
   constexpr int L = 8 / LPT;
   constexpr bool KEEP = sizeof(R) == 4 || LPT <= 4;
@@ -532,6 +690,7 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
   const bool NORM = (sizeof(R) == 4 || ALGO != ALG_OR) && (!OBS || a.update);
 
   size_t off[LPT];
+  uint32_t idx[LPT];
   bool use[LPT], gather[LPT], dn[LPT];
 #pragma unroll
   for (int j = 0; j < LPT; ++j) {
@@ -551,6 +710,7 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
       ssp = (cm > 0 ? s - st : s + (uint32_t)(nm - 1) * st) >> 1;
       par ^= 1;
     }
+    idx[j] = ssp;
     off[j] = link_off(copy, par, slot, a.NS, NC, Vh, ssp);
   }
 
@@ -573,7 +733,7 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
   for (int j = 0; j < LPT; ++j) {
     mat3<R> t;
     if (use[j]) {
-      load_rows(a.links + off[j], Vh, t);
+      load_slot<R, TILE>(stage, Gm, sp0, lane * LPT + j, idx[j], a.links + off[j], Vh, t);
       if (NORM) reproject_rows(t);
     } else {
       set_identity(t);
@@ -658,7 +818,7 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
   if (CAN_ACC && a.acc && valid && lane == 0) {
     const size_t acc_off = link_off(copy, a.parity, 4, a.NS, NC, Vh, sp);
     mat3<R> t, n;
-    load_rows(a.links + acc_off, Vh, t);
+    load_slot<R, TILE>(stage, Gm, sp0, 8, sp, a.links + acc_off, Vh, t);
     reproject_rows(t);
     reconstruct_row2(t);
     apply_left(G, t, n);
@@ -680,7 +840,7 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
     if (KEEP) {
       t = u[KEEP ? j : 0];
     } else {
-      load_rows(a.links + off[j], Vh, t);
+      load_slot<R, TILE>(stage, Gm, sp0, lane * LPT + j, idx[j], a.links + off[j], Vh, t);
       if (NORM) reproject_rows(t);
     }
     if (dn[j]) {
@@ -711,10 +871,90 @@ constexpr int min_blocks() {
                         : (LPT == 8 ? 2 : LPT >= 2 ? 1 : 2);
 }
 
+template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
+__device__ __forceinline__ void site_dispatch(const SweepArgs<R>& a, uint32_t copy, uint32_t sp, bool valid, int lane,
+                                              const float4* stage, uint32_t sp0) {
+  if constexpr (GAUGE == MAG)
+    sweep_site<R, GAUGE, ALGO, LPT, OBS>(a, copy, sp, valid, lane, stage, sp0);
+  else
+    sweep_site_k<R, GAUGE, ALGO, LPT, OBS>(a, copy, sp, valid, lane, stage, sp0);
+}
+
+// Persistent loop with two stage buffers (FP32, prefetch mode 2).  Warp 0
+// issues tile i+1's copies before the block waits for tile i's; the
+// __syncthreads at the end of an iteration frees the buffer that the next
+// iteration refills.  If a wait runs out, the block records the error, waits
+// (bounded) for the copies it issued and returns.
+template <int GAUGE, int ALGO, int LPT, bool OBS>
+__device__ __forceinline__ void sweep_staged(const SweepArgs<float>& a) {
+  constexpr int L = 8 / LPT;
+  constexpr uint32_t TILE = BLOCK / L;
+  using SG = StageGeom<TILE>;
+  extern __shared__ __align__(128) unsigned char stage_smem[];
+  float4* buf[2] = {reinterpret_cast<float4*>(stage_smem), reinterpret_cast<float4*>(stage_smem) + SG::VEC};
+  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<float4*>(stage_smem) + 2 * SG::VEC);
+  const uint32_t bar[2] = {smem_u32(&bars[0]), smem_u32(&bars[1])};
+  const uint32_t Vh = a.geom.Vh;
+  const uint32_t tiles_per_copy = (Vh + TILE - 1) / TILE;
+  const uint64_t ntiles = (uint64_t)tiles_per_copy * a.ncopies;
+  const int lane = (int)(threadIdx.x % L);
+  const uint32_t local = threadIdx.x / L;
+  const int warp = (int)(threadIdx.x >> 5), lane32 = (int)(threadIdx.x & 31);
+  if (threadIdx.x == 0) {
+    mbar_init(bar[0], 1);
+    mbar_init(bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](uint64_t t, int b) {
+    const uint32_t c = (uint32_t)(t / tiles_per_copy);
+    const uint32_t sp0 = (uint32_t)(t - (uint64_t)c * tiles_per_copy) * TILE;
+    stage_issue<GAUGE, TILE>(a, c, sp0, buf[b], bar[b], lane32);
+  };
+  uint32_t phase[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  uint64_t tile = blockIdx.x;
+  if (tile < ntiles) {
+    if (warp == 0) issue(tile, 0);
+    pending[0] = true;
+  }
+  for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+    const int b = it & 1;
+    const uint64_t next = tile + gridDim.x;
+    if (next < ntiles) {
+      if (warp == 0) issue(next, b ^ 1);
+      pending[b ^ 1] = true;
+    }
+    const bool ok = mbar_wait_bounded(bar[b], phase[b]);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        if (a.err) atomicExch(a.err, 1);
+        for (int q = 0; q < 2; ++q)
+          if (pending[q]) mbar_wait_bounded(bar[q], phase[q]);
+      }
+      __syncthreads();
+      return;
+    }
+    phase[b] ^= 1u;
+    pending[b] = false;
+    const uint32_t copy = (uint32_t)(tile / tiles_per_copy);
+    const uint32_t sp0 = (uint32_t)(tile - (uint64_t)copy * tiles_per_copy) * TILE;
+    const uint32_t sp = sp0 + local;
+    site_dispatch<float, GAUGE, ALGO, LPT, OBS>(a, copy, sp, sp < Vh, lane, buf[b], sp0);
+    __syncthreads();
+  }
+}
+
 // OBS: the variant with the fused observables (used for overrelaxation check
 // sweeps only, so that the plain kernels keep their register budget).
 template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
 __global__ void __launch_bounds__(BLOCK, min_blocks<R, GAUGE, LPT>()) sweep_kernel(const SweepArgs<R> a) {
+  if constexpr (sizeof(R) == 4) {
+    if (a.prefetch == 2) {
+      sweep_staged<GAUGE, ALGO, LPT, OBS>(a);
+      return;
+    }
+  }
   constexpr int NC = store_traits<R>::NC;
   constexpr int L = 8 / LPT;
   constexpr uint32_t TILE = BLOCK / L;
@@ -731,11 +971,8 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R, GAUGE, LPT>()) sweep_kern
       prefetch_tile<R, GAUGE>(a, nc, nsp0, min(TILE, Vh - nsp0), (int)threadIdx.x);
     }
     const uint32_t copy = (uint32_t)(tile / tiles_per_copy);
-    const uint32_t sp = (uint32_t)(tile - (uint64_t)copy * tiles_per_copy) * TILE + local;
-    if constexpr (GAUGE == MAG)
-      sweep_site<R, GAUGE, ALGO, LPT, OBS>(a, copy, sp, sp < Vh, lane);
-    else
-      sweep_site_k<R, GAUGE, ALGO, LPT, OBS>(a, copy, sp, sp < Vh, lane);
+    const uint32_t sp0 = (uint32_t)(tile - (uint64_t)copy * tiles_per_copy) * TILE;
+    site_dispatch<R, GAUGE, ALGO, LPT, OBS>(a, copy, sp0 + local, sp0 + local < Vh, lane, nullptr, sp0);
   }
 }
 

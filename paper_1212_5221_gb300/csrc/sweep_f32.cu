@@ -4,31 +4,44 @@
 
 namespace gfk {
 
-// Persistent grid: as many blocks as fit on the device at once (queried once
-// per kernel instance), each looping over tiles of BLOCK/L sites.
+// Persistent grid: as many blocks as fit on the device at once with the
+// given dynamic shared memory (queried once per kernel instance and mode),
+// each looping over tiles of BLOCK/L sites.
 template <typename K>
-static unsigned resident_blocks(K kernel) {
-  static unsigned cached = 0;
-  if (cached) return cached;
+static unsigned resident_blocks(K kernel, size_t smem) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, BLOCK, 0) != cudaSuccess || per_sm < 1) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, BLOCK, smem) != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     return 0;
   }
-  cached = (unsigned)(sms * per_sm);
-  return cached;
+  return (unsigned)(sms * per_sm);
 }
 
+// Prefetch mode 2 stages tiles in shared memory: the kernel is given the
+// two stage buffers as dynamic shared memory (above the 48 KB default, so
+// the limit is raised once per kernel instance).
 template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
 static cudaError_t launch_kernel(const SweepArgs<R>& a, cudaStream_t st) {
   constexpr uint32_t TILE = BLOCK / (8 / LPT);
   const uint64_t ntiles = (uint64_t)((a.geom.Vh + TILE - 1) / TILE) * a.ncopies;
   auto kernel = sweep_kernel<R, GAUGE, ALGO, LPT, OBS>;
-  const unsigned resident = resident_blocks(kernel);
+  constexpr size_t smem_staged = stage_smem_bytes<LPT>();
+  static const cudaError_t attr = [&] {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_staged);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+    return e;
+  }();
+  const bool staged = a.prefetch == 2;
+  if (staged && attr != cudaSuccess) return attr;
+  static const unsigned resident_plain = resident_blocks(kernel, 0);
+  static const unsigned resident_staged = attr == cudaSuccess ? resident_blocks(kernel, smem_staged) : 0;
+  const unsigned resident = staged ? resident_staged : resident_plain;
   const unsigned blocks = (unsigned)((resident && ntiles > resident) ? resident : ntiles);
-  kernel<<<blocks, BLOCK, 0, st>>>(a);
+  kernel<<<blocks, BLOCK, staged ? smem_staged : 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -8,8 +8,6 @@ namespace gfk {
 // per kernel instance), each looping over tiles of BLOCK/L sites.
 template <typename K>
 static unsigned resident_blocks(K kernel) {
-  static unsigned cached = 0;
-  if (cached) return cached;
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -17,8 +15,7 @@ static unsigned resident_blocks(K kernel) {
     cudaGetLastError();
     return 0;
   }
-  cached = (unsigned)(sms * per_sm);
-  return cached;
+  return (unsigned)(sms * per_sm);
 }
 
 template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
@@ -26,7 +23,7 @@ static cudaError_t launch_kernel(const SweepArgs<R>& a, cudaStream_t st) {
   constexpr uint32_t TILE = BLOCK / (8 / LPT);
   const uint64_t ntiles = (uint64_t)((a.geom.Vh + TILE - 1) / TILE) * a.ncopies;
   auto kernel = sweep_kernel<R, GAUGE, ALGO, LPT, OBS>;
-  const unsigned resident = resident_blocks(kernel);
+  static const unsigned resident = resident_blocks(kernel);
   const unsigned blocks = (unsigned)((resident && ntiles > resident) ? resident : ntiles);
   kernel<<<blocks, BLOCK, 0, st>>>(a);
   return cudaGetLastError();

@@ -315,8 +315,18 @@ def gf_set_links_per_thread(h, lpt):
     _check(lib().gf_set_links_per_thread(h, int(lpt)), "gf_set_links_per_thread")
 
 
-def gf_set_prefetch(h, on=True):
-    _check(lib().gf_set_prefetch(h, 1 if on else 0), "gf_set_prefetch")
+GF_PREFETCH_NONE, GF_PREFETCH_L2, GF_PREFETCH_SMEM = 0, 1, 2
+PREFETCH = {"none": 0, "l2": 1, "smem": 2}
+
+
+def gf_set_prefetch(h, mode=GF_PREFETCH_L2):
+    """How the sweep kernels fetch a block's next tile: "none" / "l2" / "smem"
+    (or 0 / 1 / 2; True means "l2", False "none")."""
+    if isinstance(mode, str):
+        mode = PREFETCH[mode]
+    elif isinstance(mode, bool):
+        mode = GF_PREFETCH_L2 if mode else GF_PREFETCH_NONE
+    _check(lib().gf_set_prefetch(h, int(mode)), "gf_set_prefetch")
 
 
 def gf_set_fused_observables(h, on=True):

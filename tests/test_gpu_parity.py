@@ -445,6 +445,73 @@ def test_lpt_variants_agree(gf, synth, orc):
         assert np.abs(o - outs[0]).max() < 5e-5
 
 
+def _prefetch_run(gf, U, gauge, prec, lpt, mode, sa):
+    with Ctx(gf, DIMS, gauge, prec, n_copies=3) as h:
+        gf.gf_set_prefetch(h, mode)
+        gf.gf_set_links_per_thread(h, lpt)
+        for k in range(3):
+            gf.gf_load_links(h, k, U)
+        gf.gf_random_gauge_transform(h, 5)
+        gf.gf_sweep(h, "or", 1.7, 2, observables=False)
+        gf.gf_sweep(h, "sr", 0.5, 1, 9, observables=False)
+        gf.gf_sweep(h, "micro", 1.0, 1, observables=False)
+        if sa:
+            gf.gf_sweep(h, "sa", 0.7, 1, 9, observables=False)
+        F, T = gf.gf_functional_theta(h)
+        return [store(gf, h, DIMS, k) for k in range(3)], F, T
+
+
+@pytest.mark.parametrize("gauge", GAUGES)
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+@pytest.mark.parametrize("lpt", [1, 2, 4, 8])
+def test_prefetch_modes_agree(gf, synth, orc, gauge, prec, lpt):
+    """The tile fetch changes where the links are read from, not what is
+    computed (3 copies, periodic wraps, ragged last tile).  Without prefetch
+    and with the L2 prefetch the same code runs: bit-identical links after
+    every algorithm.  The shared-memory-staged loop is a separately compiled
+    instance of the site update (multiply-adds may be contracted
+    differently), so it agrees within FP32 rounding; the heat bath, whose
+    FP32 trajectories are chaotic, is left out of that comparison."""
+    U = rough(synth, orc, DIMS)
+    a = _prefetch_run(gf, U, gauge, prec, lpt, "none", True)
+    b = _prefetch_run(gf, U, gauge, prec, lpt, "l2", True)
+    for x, y in zip(a[0], b[0]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    c = _prefetch_run(gf, U, gauge, prec, lpt, "l2", False)
+    d = _prefetch_run(gf, U, gauge, prec, lpt, "smem", False)
+    for x, y in zip(c[0], d[0]):
+        assert np.abs(x - y).max() <= 2e-5
+    assert np.allclose(c[1], d[1], rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("gauge", GAUGES)
+def test_prefetch_smem_fix(gf, synth, orc, gauge):
+    """A mixed-precision fix (fused checks, master syncs, FP64 tail) with
+    staged tiles converges to the same functional in about as many sweeps."""
+    U = rough(synth, orc, DIMS)
+    res = []
+    for mode in ("l2", "smem"):
+        with Ctx(gf, DIMS, gauge, "mixed") as h:
+            gf.gf_set_prefetch(h, mode)
+            gf.gf_load_links(h, 0, U)
+            r = gf.gf_fix(h, "or", 1.35 if gauge == "mag" else 1.7, 1e-12, max_sweeps=5000, check_interval=10,
+                          switch_theta=1e-9, raise_on_notconv=False)
+            F, T = gf.gf_functional_theta(h)
+            res.append((r["sweeps"], r["converged"], F[0], T[0]))
+    assert res[0][1] == res[1][1]
+    assert abs(res[0][0] - res[1][0]) <= max(20, 0.05 * res[0][0])
+    assert abs(res[0][2] - res[1][2]) <= 1e-9 * abs(res[0][2])
+
+
+def test_prefetch_mode_invalid(gf):
+    with Ctx(gf, (4, 4, 4, 4), "landau", "fp32") as h:
+        for mode in (-1, 3):
+            with pytest.raises(gf.GFError) as e:
+                gf.gf_set_prefetch(h, mode)
+            assert e.value.code == gf.GF_EINVAL
+
+
 def test_autotune_restores_links(gf, synth, orc):
     U = rough(synth, orc, (8, 8, 8, 16))
     with Ctx(gf, (8, 8, 8, 16), "landau", "fp32") as h:
