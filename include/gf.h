@@ -194,6 +194,14 @@ int gf_set_links_per_thread(gf_ctx* ctx, int lpt);
 enum { GF_PREFETCH_NONE = 0, GF_PREFETCH_L2 = 1, GF_PREFETCH_SMEM = 2 };
 int gf_set_prefetch(gf_ctx* ctx, int mode);
 
+/* Plain overrelaxation/relaxation sweeps of gf_sweep and gf_fix (those with
+ * no observables) run in blocks of 16 captured once per launch configuration
+ * as a CUDA graph and replayed (on by default; off: every kernel is launched
+ * directly; also off while profiling).  The kernels and their arguments are
+ * the same either way, and so are the results.  The graphs are captured on
+ * the context's stream in thread-local capture mode. */
+int gf_set_graphs(gf_ctx* ctx, int on);
+
 /* F and theta fused into the sweeps (on by default): the odd half of the last
  * overrelaxation/relaxation sweep -- in which every link is written exactly
  * once -- also sums F over the links it writes and theta of its sites from

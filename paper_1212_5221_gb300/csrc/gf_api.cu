@@ -7,7 +7,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -149,6 +151,12 @@ struct gf_ctx {
   std::vector<cudaEvent_t> event_pool;
   uint64_t prof_launches[GF_KERNEL_KINDS] = {0};
   double prof_ms[GF_KERNEL_KINDS] = {0};
+  // CUDA graphs of blocks of plain overrelaxation sweeps, keyed by everything
+  // their launch arguments depend on
+  bool use_graphs = true;
+  bool warm = false;  // sweep kernels launched once outside capture (one-time setup done)
+  using GraphKey = std::tuple<int, int, int, int, int, int, uint64_t, uint32_t>;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
 
   void* links() const { return fp64 ? links64 : links32; }
   int NS() const { return fp64 ? NS64 : NS32; }
@@ -291,6 +299,61 @@ int read_sweep_error(gf_ctx* c) {
     GF_CUDA(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st));
     return fail(GF_ETIMEOUT, "a shared-memory staging wait in the sweep kernel ran out");
   }
+  return GF_OK;
+}
+
+// n plain sweeps of overrelaxation / relaxation (no observables).  These
+// draw no random numbers, so every block of GRAPH_SWEEPS sweeps launches the
+// same kernels with the same arguments: it is captured once as a CUDA graph
+// and replayed, which removes the per-launch host overhead that bounds small
+// lattices.  The remainder, the first block ever (one-time kernel setup) and
+// profiled runs launch directly.
+constexpr int GRAPH_SWEEPS = 16;
+
+int plain_sweeps(gf_ctx* c, int kalgo, int api_algo, double param, int n) {
+  while (n >= GRAPH_SWEEPS && c->use_graphs && c->warm && !c->profiling) {
+    const int lpt = default_lpt(c, api_algo);
+    const int pm = c->pmode[c->fp64][api_algo] - 1;
+    const bool acc = c->prec == GF_MIXED && !c->fp64 && c->gauge != GF_COULOMB;
+    uint64_t pbits;
+    memcpy(&pbits, &param, sizeof pbits);
+    const gf_ctx::GraphKey key{c->fp64, lpt, pm >= 0 ? pm : c->prefetch, kalgo, c->all_active, acc, pbits,
+                               c->copy_base};
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+      const uint64_t idx = c->sweep_index, nl = c->launch_count;
+      if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        break;
+      }
+      int r = GF_OK;
+      for (int k = 0; k < GRAPH_SWEEPS && !r; ++k) r = full_sweep(c, kalgo, api_algo, param, 0);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(c->st, &g);
+      c->sweep_index = idx;
+      c->launch_count = nl;
+      cudaGraphExec_t x = nullptr;
+      if (r || e != cudaSuccess || !g || cudaGraphInstantiate(&x, g, 0) != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        c->use_graphs = false;  // launch directly from now on
+        if (r) return r;
+        break;
+      }
+      cudaGraphDestroy(g);
+      it = c->graphs.emplace(key, x).first;
+    }
+    GF_CUDA(cudaGraphLaunch(it->second, c->st));
+    c->sweep_index += GRAPH_SWEEPS;
+    c->launch_count += 2 * GRAPH_SWEEPS;
+    if (c->prec == GF_MIXED && !c->fp64) c->dirty = true;
+    n -= GRAPH_SWEEPS;
+  }
+  for (int k = 0; k < n; ++k) {
+    int r = full_sweep(c, kalgo, api_algo, param, 0);
+    if (r) return r;
+  }
+  if (n > 0) c->warm = true;
   return GF_OK;
 }
 
@@ -647,6 +710,7 @@ void gf_destroy(gf_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   prof_collect(c);
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
   if (c->owned) cudaFree(c->owned);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
   delete c;
@@ -762,8 +826,14 @@ int gf_sweep(gf_ctx* c, gf_algo algo, double param, int n_sweeps, uint64_t seed,
   // GF_MIXED, whose master is read instead)
   const bool fused = c->fused_obs && (F || theta) && n_sweeps > 0 && (algo == GF_OR || algo == GF_RELAX) &&
                      !(c->prec == GF_MIXED && !c->fp64);
-  for (int k = 0; k < n_sweeps; ++k)
-    if ((r = api_sweep(c, algo, param, seed, fused && k == n_sweeps - 1))) return r;
+  if ((algo == GF_OR || algo == GF_RELAX) && n_sweeps > 0) {
+    const double omega = algo == GF_RELAX ? 1.0 : param;
+    if ((r = plain_sweeps(c, gfk::ALG_OR, algo, omega, n_sweeps - 1))) return r;
+    if ((r = full_sweep(c, gfk::ALG_OR, algo, omega, seed, 0, fused))) return r;
+  } else {
+    for (int k = 0; k < n_sweeps; ++k)
+      if ((r = api_sweep(c, algo, param, seed, fused && k == n_sweeps - 1))) return r;
+  }
   if (fused) {
     std::vector<double> ct;
     if ((r = fused_observables(c, ct))) return r;
@@ -868,6 +938,13 @@ int gf_set_fused_observables(gf_ctx* c, int on) {
   int r = check_ctx(c);
   if (r) return r;
   c->fused_obs = on ? 1 : 0;
+  return GF_OK;
+}
+
+int gf_set_graphs(gf_ctx* c, int on) {
+  int r = check_ctx(c);
+  if (r) return r;
+  c->use_graphs = on != 0;
   return GF_OK;
 }
 
@@ -1047,18 +1124,28 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
     prev_worst = worst;
     prev_sweeps = R.sweeps;
     k = std::min(k, P->max_sweeps - R.sweeps);
-    for (int i = 0; i < k; ++i) {
-      const bool last = i == k - 1;
-      if ((r = api_sweep(c, P->algo, P->param, P->seed, last))) return r;
-      if (last) fused_ready = true;
-      R.site_updates += (uint64_t)n_active * sites_per_unit;
+    const int kalgo = gfk::ALG_OR;
+    const double omega = P->algo == GF_RELAX ? 1.0 : P->param;
+    for (int done = 0; done < k;) {
+      // up to the next re-unitarisation or the end of the interval, whose
+      // last sweep writes the fused observables
+      const int seg = std::min(k - done, P->reunit_interval > 0 ? P->reunit_interval - since_reunit : k - done);
+      const bool has_last = done + seg == k;
+      if ((r = plain_sweeps(c, kalgo, P->algo, omega, has_last ? seg - 1 : seg))) return r;
+      if (has_last) {
+        if ((r = full_sweep(c, kalgo, P->algo, omega, 0, 0, true))) return r;
+        fused_ready = true;
+      }
+      R.site_updates += (uint64_t)seg * n_active * sites_per_unit;
       if (c->fp64)
-        R.sweeps_fp64++;
+        R.sweeps_fp64 += seg;
       else
-        R.sweeps_fp32++;
+        R.sweeps_fp32 += seg;
+      done += seg;
       // re-unitarise (FP32, FP64) or apply the accumulated transformation to
       // the FP64 master (GF_MIXED's FP32 stage) every reunit_interval sweeps
-      if (P->reunit_interval > 0 && ++since_reunit >= P->reunit_interval) {
+      since_reunit += seg;
+      if (P->reunit_interval > 0 && since_reunit >= P->reunit_interval) {
         since_reunit = 0;
         if ((r = reunitarize(c))) return r;
         fused_ready = false;  // the links changed after the fused half-sweep

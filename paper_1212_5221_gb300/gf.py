@@ -105,6 +105,7 @@ _SIG = {
     "gf_set_copy_base": [_P, ctypes.c_uint32],
     "gf_set_links_per_thread": [_P, _I],
     "gf_set_prefetch": [_P, _I],
+    "gf_set_graphs": [_P, _I],
     "gf_set_fused_observables": [_P, _I],
     "gf_get_links_per_thread": [_P, _PI],
     "gf_autotune": [_P, _I, _PI, _PD],
@@ -317,6 +318,11 @@ def gf_set_links_per_thread(h, lpt):
 
 GF_PREFETCH_NONE, GF_PREFETCH_L2, GF_PREFETCH_SMEM = 0, 1, 2
 PREFETCH = {"none": 0, "l2": 1, "smem": 2}
+
+
+def gf_set_graphs(h, on=True):
+    """Replay blocks of plain overrelaxation sweeps as CUDA graphs (default on)."""
+    _check(lib().gf_set_graphs(h, 1 if on else 0), "gf_set_graphs")
 
 
 def gf_set_prefetch(h, mode=GF_PREFETCH_L2):

@@ -504,6 +504,33 @@ def test_prefetch_smem_fix(gf, synth, orc, gauge):
     assert abs(res[0][2] - res[1][2]) <= 1e-9 * abs(res[0][2])
 
 
+@pytest.mark.parametrize("gauge", GAUGES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+def test_graphs_bit_identical(gf, synth, orc, gauge, prec):
+    """Graph replay launches the same kernels with the same arguments: a fix
+    (per-unit stopping, re-unitarisation, precision switch) and a plain
+    gf_sweep give bit-identical links and results with graphs on and off."""
+    U = rough(synth, orc, DIMS)
+    outs = []
+    for on in (False, True):
+        with Ctx(gf, DIMS, gauge, prec, n_copies=2) as h:
+            gf.gf_set_graphs(h, on)
+            for k in range(2):
+                gf.gf_load_links(h, k, U)
+            gf.gf_random_gauge_transform(h, 4)
+            F1, T1 = gf.gf_sweep(h, "or", 1.7, 37)
+            r = gf.gf_fix(h, "or", 1.35 if gauge == "mag" else 1.7, 1e-11, max_sweeps=3000, check_interval=20,
+                          reunit_interval=50, switch_theta=1e-9, raise_on_notconv=False)
+            n = gf.gf_launch_count(h)
+            outs.append(([store(gf, h, DIMS, k) for k in range(2)], F1, T1, r["sweeps"], r["converged"], n))
+    a, b = outs
+    for x, y in zip(a[0], b[0]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    assert a[3:] == b[3:]
+    assert a[3] > 16
+
+
 def test_prefetch_mode_invalid(gf):
     with Ctx(gf, (4, 4, 4, 4), "landau", "fp32") as h:
         for mode in (-1, 3):
