@@ -142,13 +142,28 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(dims, omega, seconds_target=20.0):
-    """Time the FP64 oracle (as it stands, one thread) on whole sweeps of the
-    workload's lattice; run in a fresh process so no GPU state is shared."""
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
+
+
+def cpu_baseline(dims, omega, seconds_target=20.0, threads=1):
+    """Time the FP64 oracle on whole sweeps of the workload's lattice, in a
+    fresh process so no GPU state is shared: threads = 1 runs the plain build,
+    threads > 1 the same source built with OpenMP (the sites of a parity in
+    parallel) on that many host cores."""
     code = f"""
 import sys, time, json
 sys.path.insert(0, {ROOT!r})
 import oracle
+if {threads} > 1:
+    oracle.use_openmp()
 from paper_1212_5221_gb300 import inputs
 U = inputs.links({tuple(dims)!r}, "smooth", {WORKLOAD['eps']}, {WORKLOAD['field_seed']})
 oracle.random_gauge_transform(U, 1000)
@@ -162,16 +177,18 @@ while True:
 dt = time.time() - t0
 print(json.dumps(dict(sweeps=n, seconds=dt)))
 """
-    env = dict(os.environ, OMP_NUM_THREADS="1")
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
     if r.returncode != 0:
         log("cpu baseline failed:", r.stderr[-500:])
         return None
     d = json.loads(r.stdout.strip().splitlines()[-1])
     V = int(np.prod(dims))
-    return {"value": d["sweeps"] * V / d["seconds"], "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+    what = "single thread" if threads == 1 else f"OpenMP build, {threads} threads"
+    return {"value": d["sweeps"] * V / d["seconds"], "unit": "site-updates/s", "cores": threads, "kind": "oracle",
             "sample": f"{d['sweeps']} FP64 OR sweeps of the {'x'.join(map(str, dims[::-1]))} lattice "
-                      f"(after 1 warm-up sweep), {d['seconds']:.1f} s, single thread"}
+                      f"(after 1 warm-up sweep), {d['seconds']:.1f} s, {what}",
+            "cpu": cpu_model()}
 
 
 def reduce_over_ranks(elapsed, site_updates, device=None):
@@ -190,13 +207,19 @@ def reduce_over_ranks(elapsed, site_updates, device=None):
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 CPU oracle on this workload, rank 0 only."""
+    """Reference arm: the FP64 CPU oracle on this workload, on all host cores
+    (the OpenMP build of the same source), rank 0 only."""
     if rank != 0:
         return
     import oracle
     from paper_1212_5221_gb300 import inputs
 
-    oracle.build()
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    cores = int(os.environ["OMP_NUM_THREADS"])
+    if cores > 1:
+        oracle.use_openmp()
+    oracle.build(openmp=cores > 1)
     dims = WORKLOAD["dims"]
     V = int(np.prod(dims))
     U = inputs.links(dims, "smooth", WORKLOAD["eps"], WORKLOAD["field_seed"])
@@ -209,15 +232,16 @@ def run_reference(args, rank, world):
         oracle.sweep(U, "landau", "or", WORKLOAD["omega"], 1, args.warmup + k)
     dt = time.time() - t0
     value = args.steps * V / dt
-    sample = f"{args.steps} FP64 OR sweeps of the 32^3x64 lattice after {args.warmup} warm-up sweeps"
+    sample = (f"{args.steps} FP64 OR sweeps of the 32^3x64 lattice after {args.warmup} warm-up sweeps, "
+              f"{cores} threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "lattice": "32^3x64", "gauge": "landau", "omega": 1.7,
                        "step": "one FP64 overrelaxation sweep (oracle)"},
-            "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+                             "sample": sample, "cpu": cpu_model()},
             "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -363,7 +387,15 @@ def run_ours(args, rank, world, local_rank):
             e2e = {"value": su_e / te, "unit": "site-updates/s", "h2d_bytes_per_step": int(U.nbytes),
                    "d2h_bytes_per_step": int(U.nbytes), "steps": args.e2e_steps,
                    "seconds_per_step": te / args.e2e_steps}
-        cpu = cpu_baseline(dims, W["omega"], args.cpu_seconds) if args.cpu_seconds > 0 else None
+        # the oracle on all host cores (OpenMP build), with the single-thread figure beside it
+        cpu = None
+        if args.cpu_seconds > 0:
+            cpu = cpu_baseline(dims, W["omega"], args.cpu_seconds, threads=os.cpu_count() or 1)
+            one = cpu_baseline(dims, W["omega"], args.cpu_seconds, threads=1)
+            if cpu and one and cpu["cores"] > 1:
+                cpu["single_thread"] = {k: one[k] for k in ("value", "cores", "sample")}
+            elif one:
+                cpu = one
         mixed_tt = elapsed / args.steps
         out = {
             "metric": METRIC,

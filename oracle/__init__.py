@@ -35,23 +35,39 @@ _U32 = ctypes.c_uint32
 _U64 = ctypes.c_uint64
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, IEEE semantics, no FMA contraction)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+_openmp = False
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, IEEE semantics, no FMA contraction).
+    openmp=True: the same source with -fopenmp (the sweep visits the sites of a
+    parity in parallel), a separate library used only to time the oracle on all
+    host cores."""
+    lib = _LIB_OMP if openmp else _LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(_SRC):
+        return lib
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
     os.close(fd)
-    subprocess.run(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
-                    "-o", tmp, _SRC, "-lm"], check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    subprocess.run(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared"]
+                   + (["-fopenmp"] if openmp else []) + ["-o", tmp, _SRC, "-lm"], check=True)
+    os.replace(tmp, lib)
+    return lib
+
+
+def use_openmp():
+    """Load the OpenMP build instead of the plain one (before the first call)."""
+    global _openmp
+    if _lib is not None and not _openmp:
+        raise RuntimeError("the plain oracle library is already loaded")
+    _openmp = True
 
 
 def _load():
     global _lib
     if _lib is not None:
         return _lib
-    lib = ctypes.CDLL(build())
+    lib = ctypes.CDLL(build(openmp=_openmp))
     sig = {
         "or_philox4x32_10": (None, [ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
         "or_u01": (_D, [_U32, _U32]),

@@ -727,6 +727,10 @@ void or_sweep(const int dims[4], double* U, int gauge, int algo, double param,
   long V3 = L.V / L.n[0];
   for (int k = 0; k < n_sweeps; ++k)
     for (int p = 0; p < 2; ++p)
+      /* sites of one parity touch disjoint links (Sec. 2.2): a build with
+       * -fopenmp may visit them in parallel with the same result; the plain
+       * build ignores the pragma */
+#pragma omp parallel for schedule(static)
       for (long s = 0; s < L.V; ++s) {
         if (parity_of(&L, s) != p) continue;
         if (slice_active && !slice_active[s / V3]) continue;
