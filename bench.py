@@ -527,6 +527,110 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def unitarity(V):
+    """max and mean of max|U U^dag - 1| per link, and max|det U - 1|, of
+    natural-order links (..., 3, 3)."""
+    M = V.reshape(-1, 3, 3)
+    dev = np.empty(len(M))
+    det = np.empty(len(M))
+    for a in range(0, len(M), 1 << 20):
+        b = M[a:a + (1 << 20)]
+        P = np.einsum("nij,nkj->nik", b, b.conj()) - np.eye(3)
+        dev[a:a + len(b)] = np.abs(P).reshape(len(b), -1).max(axis=1)
+        det[a:a + len(b)] = np.abs(np.linalg.det(b) - 1)
+    return float(dev.max()), float(dev.mean()), float(det.max())
+
+
+def run_precision_study(args):
+    """Unitarity drift and functional deviation over 12000 overrelaxation
+    iterations of a 32^4 Landau problem (the shapes of Sec. 4.5's two
+    figures, on a synthetic field): FP64 with and without re-unitarisation
+    every 100 iterations, FP32 (rows re-projected at every load) with and
+    without FP64 re-unitarisation every 100, and GF_MIXED (FP64 master moved
+    by exact transformations, synced every 100)."""
+    from paper_1212_5221_gb300 import build, gf, inputs
+
+    build.build_all()
+    dims, n_iter, every = (32, 32, 32, 32), args.study_iters, args.study_every
+    U = inputs.links(dims, "smooth", 0.3, 1)
+    variants = [("fp64_reunit100", "fp64", True), ("fp64", "fp64", False), ("fp32_reunit100", "fp32", True),
+                ("fp32", "fp32", False), ("mixed", "mixed", True)]
+    V = np.empty(tuple(dims) + (4, 3, 3), np.complex128)
+    rows = {}
+    for name, prec, reunit in variants:
+        h = gf.gf_create(dims, "landau", prec)
+        gf.gf_load_links(h, 0, U)
+        gf.gf_random_gauge_transform(h, 1000)
+        series, done, t_dev = [], 0, 0.0
+        while True:
+            F, T = gf.gf_functional_theta(h)
+            gf.gf_store_links(h, 0, V)
+            umax, umean, dmax = unitarity(V)
+            series.append({"iter": done, "F": float(F[0]), "theta": float(T[0]), "unitarity_max": umax,
+                           "unitarity_mean": umean, "det_max": dmax})
+            log(name, json.dumps(series[-1]))
+            if done >= n_iter:
+                break
+            for _ in range(every // 100):
+                t0 = time.time()
+                gf.gf_sweep(h, "or", 1.7, 100, observables=False)
+                if reunit:
+                    gf.gf_reunitarize(h)
+                gf.gf_synchronize(h)
+                t_dev += time.time() - t0
+            done += every
+        gf.gf_destroy(h)
+        rows[name] = {"series": series, "seconds": t_dev}
+    ref = {r["iter"]: r["F"] for r in rows["fp64_reunit100"]["series"]}
+    for name in rows:
+        for r in rows[name]["series"]:
+            r["rel_dF_vs_fp64_reunit100"] = abs(r["F"] - ref[r["iter"]]) / abs(ref[r["iter"]])
+    print(json.dumps({"study": "precision", "lattice": "32^4", "gauge": "landau", "omega": 1.7,
+                      "field": "exp(i 0.3 H), seed 1, Haar g seed 1000", "iterations": n_iter,
+                      "variants": rows}), flush=True)
+
+
+def run_sa_temperature_study(args):
+    """Sec. 6.6's temperature scan: simulated annealing of a hot 32^4 field
+    (every link a Haar-random SU(3) matrix), 10000 steps (heat bath + three
+    microcanonical sweeps each) with T linear from 8 to 0.01, Landau and MAG,
+    mixed precision; F and theta recorded every 100 steps.  gf_anneal over a
+    chunk of 100 steps continues the same linear schedule exactly."""
+    from paper_1212_5221_gb300 import build, gf, inputs
+
+    build.build_all()
+    dims, N, chunk = (32, 32, 32, 32), args.study_iters, 100
+    T0, T1 = 8.0, 0.01
+    temp = lambda k: T0 + (T1 - T0) * k / (N - 1)
+    U = inputs.links(dims, "hot", 0.0, 7)
+    out = {}
+    for gauge in ("landau", "mag"):
+        h = gf.gf_create(dims, gauge, "mixed")
+        gf.gf_load_links(h, 0, U)
+        F, T = gf.gf_functional_theta(h)
+        series = [{"step": 0, "T": T0, "F": float(F[0]), "theta": float(T[0])}]
+        t0 = time.time()
+        for i in range(N // chunk):
+            F, T = gf.gf_anneal(h, temp(i * chunk), temp(i * chunk + chunk - 1), chunk, 17)
+            series.append({"step": (i + 1) * chunk, "T": temp(i * chunk + chunk - 1), "F": float(F[0]),
+                           "theta": float(T[0])})
+        dt = time.time() - t0
+        gf.gf_destroy(h)
+        Fs = np.array([r["F"] for r in series])
+        Ts = np.array([r["T"] for r in series])
+        dF = np.abs(np.diff(Fs))
+        k = int(np.argmax(dF))
+        gain = Fs[-1] - Fs[0]
+        t10 = float(Ts[np.argmax(Fs - Fs[0] >= 0.1 * gain)])
+        t90 = float(Ts[np.argmax(Fs - Fs[0] >= 0.9 * gain)])
+        out[gauge] = {"series": series, "seconds": dt, "sweeps": 4 * N,
+                      "site_updates_per_s": 4 * N * float(np.prod(dims)) / dt,
+                      "T_steepest": float(0.5 * (Ts[k] + Ts[k + 1])), "T_10pct_gain": t10, "T_90pct_gain": t90}
+        log(gauge, json.dumps({k2: v for k2, v in out[gauge].items() if k2 != "series"}))
+    print(json.dumps({"study": "sa_temperature", "lattice": "32^4", "field": "hot (Haar links), seed 7",
+                      "steps": N, "T": [T0, T1], "precision": "mixed", "gauges": out}), flush=True)
+
+
 def run_kernel_target(args):
     """Short, fixed launch sequences on the workload's lattice for ncu captures.
     fp32 / fp64 / mixed: 3 sweeps in that precision (mixed: FP32 sweeps that
@@ -579,7 +683,19 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-loads", type=lambda v: [float(x) for x in v.split(",") if x], default=[0.7],
                     help="Poisson rates as fractions of the measured saturated job rate")
+    ap.add_argument("--study", choices=["precision", "sa-temperature"], default=None,
+                    help="run a report study instead of the benchmark")
+    ap.add_argument("--study-iters", type=int, default=None)
+    ap.add_argument("--study-every", type=int, default=2000)
     args = ap.parse_args()
+    if args.study == "precision":
+        args.study_iters = args.study_iters or 12000
+        run_precision_study(args)
+        return
+    if args.study == "sa-temperature":
+        args.study_iters = args.study_iters or 10000
+        run_sa_temperature_study(args)
+        return
     if args.kernel_target:
         run_kernel_target(args)
         return

@@ -194,6 +194,19 @@ int gf_set_links_per_thread(gf_ctx* ctx, int lpt);
 enum { GF_PREFETCH_NONE = 0, GF_PREFETCH_L2 = 1, GF_PREFETCH_SMEM = 2 };
 int gf_set_prefetch(gf_ctx* ctx, int mode);
 
+/* Asynchronous forms of gf_sweep (without F/theta), gf_anneal and
+ * gf_random_gauge_transform: the work is enqueued on the context's stream
+ * and the call returns without waiting for it (argument errors are still
+ * returned at once).  No host buffer is involved.  gf_synchronize waits for
+ * everything enqueued on the context and returns GF_ECUDA for a device error
+ * or GF_ETIMEOUT for a shared-memory staging wait that ran out.  Every
+ * synchronous call of the context orders after the enqueued work.  A context
+ * must not be used from two threads at once. */
+int gf_sweep_async(gf_ctx* ctx, gf_algo algo, double param, int n_sweeps, uint64_t seed);
+int gf_anneal_async(gf_ctx* ctx, double T0, double T1, int n_steps, uint64_t seed);
+int gf_random_gauge_transform_async(gf_ctx* ctx, uint64_t seed);
+int gf_synchronize(gf_ctx* ctx);
+
 /* Plain overrelaxation/relaxation sweeps of gf_sweep and gf_fix (those with
  * no observables) run in blocks of 16 captured once per launch configuration
  * as a CUDA graph and replayed (on by default; off: every kernel is launched

@@ -802,7 +802,7 @@ int gf_store_links_device(gf_ctx* c, int copy, double* dev) {
   return GF_OK;
 }
 
-int gf_random_gauge_transform(gf_ctx* c, uint64_t seed) {
+int gf_random_gauge_transform_async(gf_ctx* c, uint64_t seed) {
   int r = check_ctx(c);
   if (r) return r;
   if ((r = consolidate(c))) return r;
@@ -811,9 +811,49 @@ int gf_random_gauge_transform(gf_ctx* c, uint64_t seed) {
                       : gfk::launch_haar_transform<float>(c->links32, c->G, c->NS32, c->ncopies, c->copy_base, seed, c->st);
   if (e != cudaSuccess) return fail(GF_ECUDA, "random gauge transform: %s", cudaGetErrorString(e));
   c->launch_count += 2;
-  if ((r = refresh32(c))) return r;
+  return refresh32(c);
+}
+
+int gf_random_gauge_transform(gf_ctx* c, uint64_t seed) {
+  int r = gf_random_gauge_transform_async(c, seed);
+  if (r) return r;
   GF_CUDA(cudaStreamSynchronize(c->st));
   return GF_OK;
+}
+
+int gf_sweep_async(gf_ctx* c, gf_algo algo, double param, int n_sweeps, uint64_t seed) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if ((r = check_algo_param(algo, param))) return r;
+  if (n_sweeps < 0) return fail(GF_EINVAL, "n_sweeps < 0");
+  if (algo == GF_OR || algo == GF_RELAX) {
+    if ((r = plain_sweeps(c, gfk::ALG_OR, algo, algo == GF_RELAX ? 1.0 : param, n_sweeps))) return r;
+  } else {
+    for (int k = 0; k < n_sweeps; ++k)
+      if ((r = api_sweep(c, algo, param, seed))) return r;
+  }
+  return sync_master(c);  // enqueued, as at the end of gf_sweep
+}
+
+int gf_anneal_async(gf_ctx* c, double T0, double T1, int n_steps, uint64_t seed) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!(T0 > 0) || !(T1 > 0) || !std::isfinite(T0) || !std::isfinite(T1))
+    return fail(GF_EINVAL, "temperatures must be > 0");
+  if (n_steps < 0) return fail(GF_EINVAL, "n_steps < 0");
+  for (int k = 0; k < n_steps; ++k) {
+    const double T = n_steps > 1 ? T0 + (T1 - T0) * (double)k / (double)(n_steps - 1) : T0;
+    if ((r = api_sweep(c, GF_SA, T, seed))) return r;
+  }
+  return sync_master(c);  // enqueued, as at the end of gf_anneal
+}
+
+int gf_synchronize(gf_ctx* c) {
+  int r = check_ctx(c);
+  if (r) return r;
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  prof_collect(c);
+  return read_sweep_error(c);
 }
 
 int gf_sweep(gf_ctx* c, gf_algo algo, double param, int n_sweeps, uint64_t seed, double* F, double* theta) {

@@ -106,6 +106,10 @@ _SIG = {
     "gf_set_links_per_thread": [_P, _I],
     "gf_set_prefetch": [_P, _I],
     "gf_set_graphs": [_P, _I],
+    "gf_sweep_async": [_P, _I, ctypes.c_double, _I, ctypes.c_uint64],
+    "gf_anneal_async": [_P, ctypes.c_double, ctypes.c_double, _I, ctypes.c_uint64],
+    "gf_random_gauge_transform_async": [_P, ctypes.c_uint64],
+    "gf_synchronize": [_P],
     "gf_set_fused_observables": [_P, _I],
     "gf_get_links_per_thread": [_P, _PI],
     "gf_autotune": [_P, _I, _PI, _PD],
@@ -318,6 +322,24 @@ def gf_set_links_per_thread(h, lpt):
 
 GF_PREFETCH_NONE, GF_PREFETCH_L2, GF_PREFETCH_SMEM = 0, 1, 2
 PREFETCH = {"none": 0, "l2": 1, "smem": 2}
+
+
+def gf_sweep_async(h, algo, param=1.0, n_sweeps=1, seed=0):
+    """Enqueue n sweeps on the context's stream and return (gf_synchronize waits)."""
+    _check(lib().gf_sweep_async(h, _enum(algo, ALGOS), float(param), int(n_sweeps), int(seed) & (2**64 - 1)),
+           "gf_sweep_async")
+
+
+def gf_anneal_async(h, T0, T1, n_steps, seed=0):
+    _check(lib().gf_anneal_async(h, float(T0), float(T1), int(n_steps), int(seed) & (2**64 - 1)), "gf_anneal_async")
+
+
+def gf_random_gauge_transform_async(h, seed):
+    _check(lib().gf_random_gauge_transform_async(h, int(seed) & (2**64 - 1)), "gf_random_gauge_transform_async")
+
+
+def gf_synchronize(h):
+    _check(lib().gf_synchronize(h), "gf_synchronize")
 
 
 def gf_set_graphs(h, on=True):

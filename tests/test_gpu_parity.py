@@ -531,6 +531,40 @@ def test_graphs_bit_identical(gf, synth, orc, gauge, prec):
     assert a[3] > 16
 
 
+@pytest.mark.parametrize("gauge", GAUGES)
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_async_calls_match_sync(gf, synth, orc, gauge, prec):
+    """The _async forms enqueue the same launches as the synchronous calls."""
+    U = rough(synth, orc, DIMS)
+    outs = []
+    for asy in (False, True):
+        with Ctx(gf, DIMS, gauge, prec) as h:
+            gf.gf_load_links(h, 0, U)
+            if asy:
+                gf.gf_random_gauge_transform_async(h, 3)
+                gf.gf_sweep_async(h, "or", 1.7, 25)
+                gf.gf_sweep_async(h, "sr", 0.5, 3, 7)
+                gf.gf_anneal_async(h, 1.0, 0.5, 2, 9)
+                gf.gf_synchronize(h)
+            else:
+                gf.gf_random_gauge_transform(h, 3)
+                gf.gf_sweep(h, "or", 1.7, 25, observables=False)
+                gf.gf_sweep(h, "sr", 0.5, 3, 7, observables=False)
+                gf.gf_anneal(h, 1.0, 0.5, 2, 9, observables=False)
+            outs.append(store(gf, h, DIMS))
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_async_invalid_args(gf):
+    with Ctx(gf, (4, 4, 4, 4), "landau", "fp32") as h:
+        for call in (lambda: gf.gf_sweep_async(h, "or", 2.5, 1), lambda: gf.gf_sweep_async(h, "sa", -1.0, 1),
+                     lambda: gf.gf_anneal_async(h, 0.0, 1.0, 3), lambda: gf.gf_sweep_async(h, "or", 1.7, -1)):
+            with pytest.raises(gf.GFError) as e:
+                call()
+            assert e.value.code == gf.GF_EINVAL
+        gf.gf_synchronize(h)
+
+
 def test_prefetch_mode_invalid(gf):
     with Ctx(gf, (4, 4, 4, 4), "landau", "fp32") as h:
         for mode in (-1, 3):
