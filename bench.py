@@ -631,6 +631,75 @@ def run_sa_temperature_study(args):
                       "steps": N, "T": [T0, T1], "precision": "mixed", "gauges": out}), flush=True)
 
 
+def run_fullsize_study(args):
+    """The 64^3 x 256 lattice (67M sites; eps = 0.3, seed 2, Haar g seed 2):
+    sweep throughput of Landau and Coulomb (256 time-slices in every launch)
+    in FP32, GF_MIXED and FP64, and a mixed-precision Coulomb fix to
+    theta < 1e-12 per slice (slices stop individually), at most
+    --study-iters sweeps.  The links are generated and loaded in slabs of 16
+    time-slices."""
+    import torch
+
+    from paper_1212_5221_gb300 import build, gf, inputs
+
+    build.build_all()
+    dims = (256, 64, 64, 64)
+    V = float(np.prod(dims))
+
+    # the natural-order FP64 field (38.7 GB) generated once, slab by slab, into device memory
+    dev = torch.device("cuda", 0)
+    per_t = 64 ** 3 * 4 * 18
+    src = torch.empty(dims[0] * per_t, dtype=torch.float64, device=dev)
+    for t0 in range(0, dims[0], 16):
+        slab = inputs.links(dims, "smooth", 0.3, 2, t0=t0, nt=16)
+        src[t0 * per_t:(t0 + 16) * per_t].copy_(torch.from_numpy(slab.view(np.float64).reshape(-1)))
+    torch.cuda.synchronize()
+
+    def load(h):
+        gf.gf_load_links_device(h, 0, src.data_ptr())
+        gf.gf_random_gauge_transform(h, 2)
+
+    out = {"lattice": "64^3x256", "throughput": {}}
+    for gauge in ("landau", "coulomb"):
+        for prec in ("fp32", "mixed", "fp64"):
+            need = gf.gf_footprint(dims, 1, gauge, prec)
+            if torch.cuda.mem_get_info()[0] < need + (4 << 30):
+                out["throughput"][f"{gauge}_{prec}"] = {"skipped": f"needs {need / 1e9:.1f} GB"}
+                continue
+            h = gf.gf_create(dims, gauge, prec)
+            load(h)
+            gf.gf_sweep(h, "or", 1.7, 2, observables=False)
+            gf.gf_set_profiling(h, True)
+            n = 10 if prec != "fp64" else 3
+            gf.gf_sweep(h, "or", 1.7, n, observables=False)
+            kind = 1 if prec == "fp64" else 0
+            nl, ms = gf.gf_kernel_stats(h, kind)
+            sweep_ms = ms / nl * 2
+            bpsu = {"fp32": 768, "mixed": 864, "fp64": 1536}[prec]
+            if gauge == "coulomb":
+                bpsu = bpsu * 7 // 8  # six spatial links + the accumulated g
+            out["throughput"][f"{gauge}_{prec}"] = {
+                "ms_per_sweep": sweep_ms, "site_updates_per_s": V / (sweep_ms / 1e3),
+                "hbm_gbs": V * bpsu / (sweep_ms / 1e3) / 1e9, "footprint_gb": need / 1e9}
+            log(gauge, prec, json.dumps(out["throughput"][f"{gauge}_{prec}"]))
+            gf.gf_destroy(h)
+    h = gf.gf_create(dims, "coulomb", "mixed")
+    load(h)
+    t0 = time.time()
+    r = gf.gf_fix(h, "or", 1.7, 1e-12, max_sweeps=args.study_iters, check_interval=20, reunit_interval=100,
+                  switch_theta=1e-13, raise_on_notconv=False)
+    dt = time.time() - t0
+    Ft, Tt = gf.gf_slice_functional_theta(h)
+    gf.gf_destroy(h)
+    out["coulomb_fix_mixed"] = {"seconds": dt, "sweeps": r["sweeps"], "sweeps_fp32": r["sweeps_fp32"],
+                                "sweeps_fp64": r["sweeps_fp64"], "converged": r["converged"],
+                                "site_updates_per_s": r["site_updates"] / dt,
+                                "slices_below_1e-12": int((Tt[0] < 1e-12).sum()), "theta_max": float(Tt[0].max()),
+                                "F_mean": float(Ft[0].mean())}
+    log("coulomb fix", json.dumps(out["coulomb_fix_mixed"]))
+    print(json.dumps({"study": "fullsize", **out}), flush=True)
+
+
 def run_kernel_target(args):
     """Short, fixed launch sequences on the workload's lattice for ncu captures.
     fp32 / fp64 / mixed: 3 sweeps in that precision (mixed: FP32 sweeps that
@@ -683,7 +752,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-loads", type=lambda v: [float(x) for x in v.split(",") if x], default=[0.7],
                     help="Poisson rates as fractions of the measured saturated job rate")
-    ap.add_argument("--study", choices=["precision", "sa-temperature"], default=None,
+    ap.add_argument("--study", choices=["precision", "sa-temperature", "fullsize"], default=None,
                     help="run a report study instead of the benchmark")
     ap.add_argument("--study-iters", type=int, default=None)
     ap.add_argument("--study-every", type=int, default=2000)
@@ -691,6 +760,10 @@ def main():
     if args.study == "precision":
         args.study_iters = args.study_iters or 12000
         run_precision_study(args)
+        return
+    if args.study == "fullsize":
+        args.study_iters = args.study_iters or 8000
+        run_fullsize_study(args)
         return
     if args.study == "sa-temperature":
         args.study_iters = args.study_iters or 10000

@@ -675,7 +675,10 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
   constexpr uint32_t TILE = BLOCK / (8 / LPT);
   constexpr int NC = store_traits<R>::NC;
   constexpr int L = 8 / LPT;
-  constexpr bool KEEP = sizeof(R) == 4 || LPT <= 4;
+  // The links are held in registers between the gather and the update, except
+  // for FP64 with eight links per lane and the fused-observables variants,
+  // which read them again (from L2) instead of spilling
+  constexpr bool KEEP = sizeof(R) == 4 ? !OBS : LPT <= 4;
   const Geom& Gm = a.geom;
   const uint32_t Vh = Gm.Vh;
   int c[4] = {0, 0, 0, 0};
@@ -859,16 +862,17 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
   }
 }
 
-// Resident blocks per SM requested from the register allocator: FP32 keeps
-// 2-4 blocks of 256 threads per SM (<= 128 / 85 / 64 registers).  FP64 in K
-// form fits two blocks with eight links per lane (the links are read again
-// for the update) and one with four or two (links held in registers); the
-// per-slot MAG form needs the whole register file for four or eight.
+// Resident blocks per SM requested from the register allocator (blocks of
+// 256 threads; 1 / 2 / 3 / 4 blocks allow 255 / 128 / 80 / 64 registers):
+// FP32 1 / 2 / 3 / 4 blocks for 8 / 4 / 2 / 1 links per lane.  FP64 in K form
+// 2 / 1 / 1 / 2 (eight links per lane read the links again for the update);
+// the per-slot MAG form 1 / 1 / 2 / 3.  (Reading the links again in FP32 as
+// well, to fit one more block, measured slower: 0.347 against 0.324 ms per
+// 32^3 x 64 sweep.)
 template <typename R, int GAUGE, int LPT>
 constexpr int min_blocks() {
-  return sizeof(R) == 4 ? (LPT == 8 ? 1 : LPT == 4 ? 2 : LPT == 2 ? 3 : 4)
-         : GAUGE == MAG ? (LPT >= 4 ? 1 : LPT == 2 ? 2 : 3)
-                        : (LPT == 8 ? 2 : LPT >= 2 ? 1 : 2);
+  if (sizeof(R) == 4) return LPT == 8 ? 1 : LPT == 4 ? 2 : LPT == 2 ? 3 : 4;
+  return GAUGE == MAG ? (LPT >= 4 ? 1 : LPT == 2 ? 2 : 3) : (LPT == 8 ? 2 : LPT >= 2 ? 1 : 2);
 }
 
 template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
