@@ -70,7 +70,8 @@ enum {
   GF_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
   GF_ETIMEOUT = 4,   /* a bounded wait expired */
   GF_ENOTCONV = 5,   /* gf_fix: the sweep limit was reached before theta_target */
-  GF_ENOSYS = 6      /* the library was built without a usable CUDA device */
+  GF_ENOSYS = 6,     /* the library was built without a usable CUDA device */
+  GF_ECANCELED = 7   /* a served job removed from the queue by gf_server_cancel */
 };
 
 /* Bytes of device memory a context needs (links in the storage layout,
@@ -215,6 +216,14 @@ int gf_synchronize(gf_ctx* ctx);
  * the context's stream in thread-local capture mode. */
 int gf_set_graphs(gf_ctx* ctx, int on);
 
+/* Append one JSON line per convergence check of gf_fix and gf_protocol to
+ * the file at path (created if missing): the call, the check number, sweeps
+ * so far, the storage the sweeps ran on ("fp32" / "fp64"), the worst and the
+ * mean theta of the units still active, the mean F, the number of active
+ * units and the elapsed seconds.  path NULL stops logging.  GF_EINVAL if the
+ * file cannot be opened. */
+int gf_set_check_log(gf_ctx* ctx, const char* path);
+
 /* F and theta fused into the sweeps (on by default): the odd half of the last
  * overrelaxation/relaxation sweep -- in which every link is written exactly
  * once -- also sums F over the links it writes and theta of its sites from
@@ -230,6 +239,9 @@ int gf_get_links_per_thread(gf_ctx* ctx, int* lpt);
  * links, restore them, and keep the fastest for (storage precision, algo).
  * A later gf_set_prefetch replaces the tuned tile fetch. */
 int gf_autotune(gf_ctx* ctx, gf_algo algo, int* best_lpt, double* ms_per_sweep_best);
+/* The choice is also kept for the process, per (gauge, storage precision,
+ * algorithm, lattice class = floor(log2(sites x copies))): contexts created
+ * later start from it (a job server tunes each class once). */
 
 /* Drive the sweeps to theta < theta_target (the while-loop of Alg. 1).
  * theta is evaluated every check_interval sweeps; a unit (a copy, or for
@@ -385,6 +397,11 @@ int gf_server_submit(gf_server* server, const gf_job* job);
 int gf_server_poll(gf_server* server, gf_job_result* out, int max_results, int wait_ms, int* n_out);
 
 int gf_server_status(gf_server* server, int* queued, int* running, uint64_t* completed, size_t* bytes_in_use);
+
+/* Remove the queued (not yet admitted) jobs with this tag; each is reported
+ * by gf_server_poll with status GF_ECANCELED.  A job already running runs to
+ * completion.  *n_canceled receives the number removed (0 is not an error). */
+int gf_server_cancel(gf_server* server, uint64_t tag, int* n_canceled);
 
 /* Runs every queued job to completion, then releases the arena. */
 void gf_server_destroy(gf_server* server);

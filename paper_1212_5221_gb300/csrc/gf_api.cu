@@ -8,10 +8,13 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <tuple>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "gf.h"
 #include "gf_sweep.cuh"
@@ -44,6 +47,31 @@ constexpr size_t ALIGN = 256;
 constexpr size_t STAGING_BYTES = (size_t)256 << 20;
 
 size_t round_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+// NVTX range around a host phase (shown by Nsight tools; no cost without one)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+
+// Launch parameters chosen by gf_autotune, kept for the process per
+// (gauge, storage is FP64, algorithm, floor(log2(sites x copies))).
+struct Tuned {
+  int lpt, pmode;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, Tuned> g_tuned;
+
+int volume_class(uint64_t v) {
+  int k = 0;
+  while (v > 1) {
+    v >>= 1;
+    ++k;
+  }
+  return k;
+}
 
 struct Layout {
   size_t links32 = 0, links64 = 0, gscratch = 0, obs_site = 0, active = 0, partial = 0, obs = 0, err = 0,
@@ -157,6 +185,7 @@ struct gf_ctx {
   bool warm = false;  // sweep kernels launched once outside capture (one-time setup done)
   using GraphKey = std::tuple<int, int, int, int, int, int, uint64_t, uint32_t>;
   std::map<GraphKey, cudaGraphExec_t> graphs;
+  FILE* check_log = nullptr;  // JSON lines, one per convergence check
 
   void* links() const { return fp64 ? links64 : links32; }
   int NS() const { return fp64 ? NS64 : NS32; }
@@ -550,6 +579,18 @@ int create_impl(const int dims[4], int ncopies, int gauge, int prec, void* strea
     gf_destroy(c);
     return r;
   }
+  {  // start from the launch parameters tuned earlier for this lattice class
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    const int vc = volume_class((uint64_t)c->G.V * (uint64_t)c->ncopies);
+    for (int f64 = 0; f64 < 2; ++f64)
+      for (int a = 0; a < 5; ++a) {
+        auto it = g_tuned.find(std::make_tuple(c->gauge, f64, a, vc));
+        if (it != g_tuned.end()) {
+          c->lpt[f64][a] = it->second.lpt;
+          c->pmode[f64][a] = it->second.pmode + 1;
+        }
+      }
+  }
   *out = c;
   return GF_OK;
 }
@@ -711,6 +752,7 @@ void gf_destroy(gf_ctx* c) {
   prof_collect(c);
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
+  if (c->check_log) fclose(c->check_log);
   if (c->owned) cudaFree(c->owned);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
   delete c;
@@ -981,6 +1023,17 @@ int gf_set_fused_observables(gf_ctx* c, int on) {
   return GF_OK;
 }
 
+int gf_set_check_log(gf_ctx* c, const char* path) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (c->check_log) fclose(c->check_log);
+  c->check_log = nullptr;
+  if (!path) return GF_OK;
+  c->check_log = fopen(path, "a");
+  if (!c->check_log) return fail(GF_EINVAL, "cannot open %s for appending", path);
+  return GF_OK;
+}
+
 int gf_set_graphs(gf_ctx* c, int on) {
   int r = check_ctx(c);
   if (r) return r;
@@ -1067,9 +1120,25 @@ int gf_autotune(gf_ctx* c, gf_algo algo, int* best_lpt, double* ms_best) {
   if (r) return r;
   c->lpt[c->fp64][algo] = best;
   c->pmode[c->fp64][algo] = best_mode + 1;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[std::make_tuple(c->gauge, (int)c->fp64, (int)algo,
+                            volume_class((uint64_t)c->G.V * (uint64_t)c->ncopies))] = Tuned{best, best_mode};
+  }
   if (best_lpt) *best_lpt = best;
   if (ms_best) *ms_best = best_ms;
   return GF_OK;
+}
+
+// One JSON line per convergence check (gf_set_check_log).
+void log_check(gf_ctx* c, const char* call, int check, int sweeps, double worst, double theta_mean, double F_mean,
+               int active, double seconds) {
+  if (!c->check_log) return;
+  fprintf(c->check_log,
+          "{\"call\": \"%s\", \"check\": %d, \"sweeps\": %d, \"storage\": \"%s\", \"theta_worst\": %.6e, "
+          "\"theta_mean\": %.6e, \"F_mean\": %.15f, \"active_units\": %d, \"seconds\": %.6f}\n",
+          call, check, sweeps, c->fp64 ? "fp64" : "fp32", worst, theta_mean, F_mean, active, seconds);
+  fflush(c->check_log);
 }
 
 int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
@@ -1081,6 +1150,7 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
   if (!(P->theta_target > 0)) return fail(GF_EINVAL, "theta_target must be > 0");
   if (P->max_sweeps < 0 || P->check_interval < 1 || P->reunit_interval < 0)
     return fail(GF_EINVAL, "bad sweep counts");
+  Range range_fix("gf_fix");
   const auto t_start = std::chrono::steady_clock::now();
   gf_fix_result R;
   memset(&R, 0, sizeof R);
@@ -1100,7 +1170,10 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
   for (;;) {
     // theta after the last sweep: fused into its odd half when nothing has
     // touched the links since, else the standalone pass
-    if ((r = (fused_ready && c->fused_obs) ? fused_observables(c, ct) : observables(c, ct))) return r;
+    {
+      Range range_check("check");
+      if ((r = (fused_ready && c->fused_obs) ? fused_observables(c, ct) : observables(c, ct))) return r;
+    }
     fused_ready = false;
     R.checks++;
     // theta per unit: a copy (Landau/MAG, mean over slices) or a time-slice (Coulomb)
@@ -1131,6 +1204,19 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
           worst = std::max(worst, th);
         }
       }
+    if (c->check_log) {
+      double Fm = 0, Tm = 0;
+      int nu = 0;
+      for (int k = 0; k < c->ncopies; ++k)
+        for (int t = 0; t < Nt; ++t) Fm += ct[2 * ((size_t)k * Nt + t)];
+      for (size_t u = 0; u < unit_theta.size(); ++u)
+        if (c->gauge == GF_COULOMB ? c->active_h[u] : c->active_h[u * Nt]) {
+          Tm += unit_theta[u];
+          ++nu;
+        }
+      log_check(c, "gf_fix", R.checks, R.sweeps, worst, nu ? Tm / nu : 0.0, Fm / ((double)c->ncopies * Nt), n_active,
+                std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+    }
     if ((r = upload_active(c))) return r;
     if (n_active == 0) {
       R.converged = 1;
@@ -1149,6 +1235,7 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
       const bool stalled = worst < std::max(100.0 * P->switch_theta, 1e-9) &&
                            R.sweeps - best_at >= 25 * P->check_interval;
       if (worst < P->switch_theta || stalled || !std::isfinite(worst)) {
+        Range range_promote("switch to FP64");
         if ((r = promote(c))) return r;
         prev_worst = -1.0;
         continue;  // re-evaluate theta in FP64 (standalone pass)
@@ -1171,6 +1258,7 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
       // last sweep writes the fused observables
       const int seg = std::min(k - done, P->reunit_interval > 0 ? P->reunit_interval - since_reunit : k - done);
       const bool has_last = done + seg == k;
+      Range range_sweeps(c->fp64 ? "sweeps fp64" : "sweeps fp32");
       if ((r = plain_sweeps(c, kalgo, P->algo, omega, has_last ? seg - 1 : seg))) return r;
       if (has_last) {
         if ((r = full_sweep(c, kalgo, P->algo, omega, 0, 0, true))) return r;
@@ -1215,17 +1303,22 @@ int gf_protocol(gf_ctx* c, const gf_protocol_params* P, gf_fix_result* res) {
   const uint64_t sites = (uint64_t)c->ncopies * c->G.V;
   // 1. simulated annealing: heat bath + three microcanonical sweeps per step,
   //    T linear from T_start to T_end (Sec. 2.3)
-  for (int k = 0; k < P->sa_steps; ++k) {
-    const double T = P->sa_steps > 1 ? P->T_start + (P->T_end - P->T_start) * k / (double)(P->sa_steps - 1)
-                                     : P->T_start;
-    if ((r = api_sweep(c, GF_SA, T, P->seed))) return r;
-    R.sweeps += 4;
-    R.site_updates += 4 * sites;
-    if (c->prec != GF_FP64 && !c->fp64) {
-      R.sweeps_fp32 += 4;
-      if (P->fix.reunit_interval > 0 && (k + 1) * 4 % P->fix.reunit_interval < 4 && (r = reunitarize(c))) return r;
-    } else {
-      R.sweeps_fp64 += 4;
+  Range range_protocol("gf_protocol");
+  {
+    Range range_sa("simulated annealing");
+    for (int k = 0; k < P->sa_steps; ++k) {
+      const double T = P->sa_steps > 1 ? P->T_start + (P->T_end - P->T_start) * k / (double)(P->sa_steps - 1)
+                                       : P->T_start;
+      if ((r = api_sweep(c, GF_SA, T, P->seed))) return r;
+      R.sweeps += 4;
+      R.site_updates += 4 * sites;
+      if (c->prec != GF_FP64 && !c->fp64) {
+        R.sweeps_fp32 += 4;
+        if (P->fix.reunit_interval > 0 && (k + 1) * 4 % P->fix.reunit_interval < 4 && (r = reunitarize(c)))
+          return r;
+      } else {
+        R.sweeps_fp64 += 4;
+      }
     }
   }
   // 2. stochastic relaxation until every copy has theta < sr_theta or
@@ -1236,10 +1329,25 @@ int gf_protocol(gf_ctx* c, const gf_protocol_params* P, gf_fix_result* res) {
   // a copy leaves the SR phase at the first check with theta < sr_theta, so a
   // copy's trajectory is the same alone and in a batch
   const int Nt = c->dims[0];
+  Range range_sr("stochastic relaxation");
   while (done < P->sr_sweeps) {
     if ((r = observables(c, ct))) return r;
     R.checks++;
     copy_means(c, ct, Fc.data(), Tc.data());
+    if (c->check_log) {
+      double Fm = 0, Tm = 0, Tw = 0;
+      int na = 0;
+      for (int k = 0; k < c->ncopies; ++k) {
+        Fm += Fc[k];
+        if (c->active_h[(size_t)k * Nt] && Tc[k] >= P->sr_theta) {
+          Tm += Tc[k];
+          Tw = std::max(Tw, Tc[k]);
+          ++na;
+        }
+      }
+      log_check(c, "gf_protocol", R.checks, R.sweeps_fp32 + R.sweeps_fp64, Tw, na ? Tm / na : 0.0,
+                Fm / c->ncopies, na, std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+    }
     int n_active = 0;
     for (int k = 0; k < c->ncopies; ++k) {
       const int v = (c->active_h[(size_t)k * Nt] && Tc[k] >= P->sr_theta) ? 1 : 0;
@@ -1356,6 +1464,7 @@ const char* gf_strerror(int status) {
     case GF_ETIMEOUT: return "GF_ETIMEOUT: bounded wait expired";
     case GF_ENOTCONV: return "GF_ENOTCONV: not converged";
     case GF_ENOSYS: return "GF_ENOSYS: no CUDA device";
+    case GF_ECANCELED: return "GF_ECANCELED: job canceled";
   }
   return "unknown status";
 }

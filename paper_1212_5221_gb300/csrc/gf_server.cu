@@ -20,6 +20,8 @@
 
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gf.h"
 #include "gf_launch.h"
 
@@ -120,6 +122,7 @@ int sfail(int code, const char* msg) {
 
 // Run one admitted job on its own context carved from the arena block.
 void run_job(gf_server* S, const gf_job& J, char* mem, size_t bytes, gf_job_result& R) {
+  nvtxRangePushA("server job");
   gf_ctx* c = nullptr;
   int r = gf_create_ext(J.dims, 1, J.gauge, J.prec, nullptr, mem, bytes, &c);
   if (!r) r = gf_load_links(c, 0, J.host_links);
@@ -140,6 +143,7 @@ void run_job(gf_server* S, const gf_job& J, char* mem, size_t bytes, gf_job_resu
   R.sweeps_fp64 = fr.sweeps_fp64;
   R.site_updates = fr.site_updates;
   gf_destroy(c);
+  nvtxRangePop();
 }
 
 void worker_main(gf_server* S) {
@@ -280,6 +284,37 @@ int gf_server_status(gf_server* S, int* queued, int* running, uint64_t* complete
   if (running) *running = S->running;
   if (completed) *completed = S->n_done_total;
   if (bytes_in_use) *bytes_in_use = S->arena->used();
+  return GF_OK;
+}
+
+int gf_server_cancel(gf_server* S, uint64_t tag, int* n_canceled) {
+  if (!S) return sfail(GF_EINVAL, "NULL server");
+  int n = 0;
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    for (auto it = S->queue.begin(); it != S->queue.end();) {
+      if (it->job.tag != tag) {
+        ++it;
+        continue;
+      }
+      gf_job_result R;
+      memset(&R, 0, sizeof R);
+      R.tag = tag;
+      R.status = GF_ECANCELED;
+      R.footprint = it->bytes;
+      R.t_submit = it->t_submit;
+      R.t_admit = R.t_done = S->now();
+      S->done.push_back(R);
+      S->n_done_total++;
+      it = S->queue.erase(it);
+      ++n;
+    }
+  }
+  if (n) {
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();  // a large job at the head may have been blocking others
+  }
+  if (n_canceled) *n_canceled = n;
   return GF_OK;
 }
 

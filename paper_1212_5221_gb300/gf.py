@@ -24,7 +24,7 @@ GF_LANDAU, GF_COULOMB, GF_MAG = 0, 1, 2
 GF_FP64, GF_FP32, GF_MIXED = 0, 1, 2
 GF_RELAX, GF_OR, GF_MICRO, GF_SR, GF_SA = 0, 1, 2, 3, 4
 GF_KERNEL_SWEEP_FP32, GF_KERNEL_SWEEP_FP64, GF_KERNEL_OBSERVABLES, GF_KERNEL_REUNITARIZE, GF_KERNEL_OTHER = range(5)
-GF_OK, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_ETIMEOUT, GF_ENOTCONV, GF_ENOSYS = range(7)
+GF_OK, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_ETIMEOUT, GF_ENOTCONV, GF_ENOSYS, GF_ECANCELED = range(8)
 
 GAUGES = {"landau": GF_LANDAU, "coulomb": GF_COULOMB, "mag": GF_MAG}
 PRECISIONS = {"fp64": GF_FP64, "fp32": GF_FP32, "mixed": GF_MIXED}
@@ -106,6 +106,7 @@ _SIG = {
     "gf_set_links_per_thread": [_P, _I],
     "gf_set_prefetch": [_P, _I],
     "gf_set_graphs": [_P, _I],
+    "gf_set_check_log": [_P, ctypes.c_char_p],
     "gf_sweep_async": [_P, _I, ctypes.c_double, _I, ctypes.c_uint64],
     "gf_anneal_async": [_P, ctypes.c_double, ctypes.c_double, _I, ctypes.c_uint64],
     "gf_random_gauge_transform_async": [_P, ctypes.c_uint64],
@@ -126,6 +127,7 @@ _SIG = {
     "gf_server_submit": [_P, ctypes.POINTER(gf_job)],
     "gf_server_poll": [_P, _P, _I, _I, _PI],
     "gf_server_status": [_P, _PI, _PI, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_size_t)],
+    "gf_server_cancel": [_P, ctypes.c_uint64, _PI],
 }
 _lib = None
 
@@ -342,6 +344,11 @@ def gf_synchronize(h):
     _check(lib().gf_synchronize(h), "gf_synchronize")
 
 
+def gf_set_check_log(h, path):
+    """Append one JSON line per convergence check of gf_fix / gf_protocol to path (None stops)."""
+    _check(lib().gf_set_check_log(h, None if path is None else os.fsencode(path)), "gf_set_check_log")
+
+
 def gf_set_graphs(h, on=True):
     """Replay blocks of plain overrelaxation sweeps as CUDA graphs (default on)."""
     _check(lib().gf_set_graphs(h, 1 if on else 0), "gf_set_graphs")
@@ -483,6 +490,13 @@ def gf_server_status(s):
     _check(lib().gf_server_status(s, ctypes.byref(q), ctypes.byref(r), ctypes.byref(c), ctypes.byref(b)),
            "gf_server_status")
     return dict(queued=q.value, running=r.value, completed=c.value, bytes_in_use=b.value)
+
+
+def gf_server_cancel(s, tag):
+    """Remove the queued jobs with this tag (reported with GF_ECANCELED); returns how many."""
+    n = ctypes.c_int()
+    _check(lib().gf_server_cancel(s, int(tag), ctypes.byref(n)), "gf_server_cancel")
+    return n.value
 
 
 def gf_server_destroy(s):

@@ -565,6 +565,40 @@ def test_async_invalid_args(gf):
         gf.gf_synchronize(h)
 
 
+def test_check_log(gf, synth, orc, tmp_path):
+    """gf_set_check_log: one JSON line per check of gf_fix, the last one with
+    the final sweep count and no active unit."""
+    import json
+
+    U = rough(synth, orc, DIMS)
+    path = tmp_path / "checks.jsonl"
+    with Ctx(gf, DIMS, "coulomb", "mixed") as h:
+        gf.gf_set_check_log(h, str(path))
+        gf.gf_load_links(h, 0, U)
+        r = gf.gf_fix(h, "or", 1.7, 1e-12, max_sweeps=5000, check_interval=10, switch_theta=1e-9)
+        gf.gf_set_check_log(h, None)
+    lines = [json.loads(x) for x in path.read_text().splitlines()]
+    assert len(lines) == r["checks"]
+    assert [x["check"] for x in lines] == list(range(1, r["checks"] + 1))
+    assert lines[-1]["sweeps"] == r["sweeps"] and lines[-1]["active_units"] == 0
+    assert lines[0]["storage"] == "fp32" and lines[-1]["storage"] == "fp64"
+    assert all(x["call"] == "gf_fix" for x in lines)
+    assert all(a["sweeps"] <= b["sweeps"] for a, b in zip(lines, lines[1:]))
+
+
+def test_autotune_choice_carries_to_new_contexts(gf, synth, orc):
+    """A context created after gf_autotune on the same (gauge, storage,
+    lattice class) starts from the tuned links-per-thread."""
+    U = rough(synth, orc, (8, 8, 8, 16))
+    with Ctx(gf, (8, 8, 8, 16), "mag", "fp32") as h:
+        gf.gf_load_links(h, 0, U)
+        best, _ = gf.gf_autotune(h, "or")
+    with Ctx(gf, (8, 8, 16, 8), "mag", "fp32") as h:  # same volume class
+        assert gf.gf_get_links_per_thread(h) == best
+        gf.gf_load_links(h, 0, np.ascontiguousarray(rough(synth, orc, (8, 8, 16, 8))))
+        gf.gf_sweep(h, "or", 1.35, 2, observables=False)
+
+
 def test_prefetch_mode_invalid(gf):
     with Ctx(gf, (4, 4, 4, 4), "landau", "fp32") as h:
         for mode in (-1, 3):

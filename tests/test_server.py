@@ -63,3 +63,29 @@ def test_mock_server_destroy_drains_queue(gf):
     for k in range(4):
         gf.gf_server_submit(s, (8, 8, 8, 8), "mag", "fp32", tag=k)
     gf.gf_server_destroy(s)  # returns after running all four
+
+
+def test_mock_server_cancel(gf):
+    """Queued jobs can be canceled (reported with GF_ECANCELED); a running job
+    completes; an unknown tag cancels nothing."""
+    dims = (8, 8, 8, 8)
+    s = gf.gf_server_create_mock(_fp(gf, dims) + 4096, 1, 0.5 / (_fp(gf, dims) / 1e9))  # 0.5 s per job
+    try:
+        for tag in (1, 2, 3, 3):
+            gf.gf_server_submit(s, dims, "landau", "mixed", tag=tag)
+        t0 = time.time()
+        while gf.gf_server_status(s)["running"] == 0 and time.time() - t0 < 10:
+            time.sleep(0.01)
+        assert gf.gf_server_cancel(s, 3) == 2
+        assert gf.gf_server_cancel(s, 99) == 0
+        res = []
+        while len(res) < 4 and time.time() - t0 < 30:
+            res += gf.gf_server_poll(s, 64, 100)
+        by = {}
+        for r in res:
+            by.setdefault(r["tag"], []).append(r["status"])
+        assert by[3] == [gf.GF_ECANCELED, gf.GF_ECANCELED]
+        assert by[1] == [0] and by[2] == [0]
+        assert gf.gf_server_status(s)["completed"] == 4
+    finally:
+        gf.gf_server_destroy(s)
