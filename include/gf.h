@@ -195,6 +195,14 @@ int gf_set_links_per_thread(gf_ctx* ctx, int lpt);
 enum { GF_PREFETCH_NONE = 0, GF_PREFETCH_L2 = 1, GF_PREFETCH_SMEM = 2 };
 int gf_set_prefetch(gf_ctx* ctx, int mode);
 
+/* Polls of a GF_PREFETCH_SMEM staging wait before it gives up: polls < 0
+ * restores the default (2^24 polls, about 2 s); polls = 0 makes the first
+ * wait of every block run out at once.  The latter exists to exercise the
+ * timeout path: the blocks then wait (bounded) for the copies they issued,
+ * return without updating their tiles, and the next call that reads results
+ * back reports GF_ETIMEOUT; the context stays usable. */
+int gf_set_stage_wait_polls(gf_ctx* ctx, int polls);
+
 /* Asynchronous forms of gf_sweep (without F/theta), gf_anneal and
  * gf_random_gauge_transform: the work is enqueued on the context's stream
  * and the call returns without waiting for it (argument errors are still

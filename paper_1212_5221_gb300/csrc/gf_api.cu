@@ -165,6 +165,7 @@ struct gf_ctx {
   uint64_t sweep_index = 0;
   uint32_t copy_base = 0;  // Philox copy id of copy 0
   int prefetch = GF_PREFETCH_L2;  // how the sweep kernels fetch the next tile
+  int stage_wait_polls = -1;      // polls of a staging wait (< 0: the kernel's default)
   int fused_obs = 1;       // F/theta fused into the last OR sweep where possible
   int lpt[2][5] = {{0}};  // [fp64][algo] chosen links per thread, 0 = default
   int pmode[2][5] = {{0}};  // [fp64][algo] tile fetch chosen by gf_autotune + 1, 0 = the context's
@@ -267,6 +268,7 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     a.update = update;
     a.obs_site = static_cast<double2*>(c->obs_site);
     a.err = c->err_d;
+    a.wait_polls = -1;
     cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<double>(a, c->gauge, kalgo, lpt, c->st);
     prof_end(c, t0, GF_KERNEL_SWEEP_FP64);
@@ -290,6 +292,7 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     a.update = update;
     a.obs_site = static_cast<double2*>(c->obs_site);
     a.err = c->err_d;
+    a.wait_polls = c->stage_wait_polls;
     if (a.prefetch == GF_PREFETCH_SMEM) c->err_pending = true;
     cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<float>(a, c->gauge, kalgo, lpt, c->st);
@@ -1031,6 +1034,13 @@ int gf_set_check_log(gf_ctx* c, const char* path) {
   if (!path) return GF_OK;
   c->check_log = fopen(path, "a");
   if (!c->check_log) return fail(GF_EINVAL, "cannot open %s for appending", path);
+  return GF_OK;
+}
+
+int gf_set_stage_wait_polls(gf_ctx* c, int polls) {
+  int r = check_ctx(c);
+  if (r) return r;
+  c->stage_wait_polls = polls < 0 ? -1 : polls;
   return GF_OK;
 }
 

@@ -28,6 +28,8 @@ struct SweepArgs {
   int update;         // 0: read-only pass (with obs = 1): gather, no update, no store
   double2* obs_site;  // [copy][site] (F, theta) contributions written by lane 0
   int* err;           // set to 1 if a shared-memory staging wait ran out (prefetch 2)
+  int wait_polls;     // polls of a staging wait before it gives up: < 0 the default
+                      // (2^24, about 2 s), 0 none (the wait runs out at once)
 };
 
 // Per-site FP64 observables from the slot matrices M (M = U_mu(x) for up
@@ -301,10 +303,11 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 // Wait for the phase with the given parity to complete, for at most about
-// two seconds (and 2^24 polls); false if it did not.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// two seconds and max_polls polls; false if it did not.
+constexpr uint32_t WAIT_POLLS = 1u << 24;
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint32_t max_polls = WAIT_POLLS) {
   const uint64_t t0 = globaltimer_ns();
-  for (uint32_t i = 0; i < (1u << 24); ++i) {
+  for (uint32_t i = 0; i < max_polls; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 63u) == 63u && globaltimer_ns() - t0 > 2000000000ull) return false;
   }
@@ -929,8 +932,10 @@ __device__ __forceinline__ void sweep_staged(const SweepArgs<float>& a) {
       if (warp == 0) issue(next, b ^ 1);
       pending[b ^ 1] = true;
     }
-    const bool ok = mbar_wait_bounded(bar[b], phase[b]);
+    const bool ok = mbar_wait_bounded(bar[b], phase[b], a.wait_polls < 0 ? WAIT_POLLS : (uint32_t)a.wait_polls);
     if (__syncthreads_or(!ok)) {
+      // the copies issued for this tile and the next are waited for with the
+      // full bound before the block leaves (none may land after it exits)
       if (threadIdx.x == 0) {
         if (a.err) atomicExch(a.err, 1);
         for (int q = 0; q < 2; ++q)

@@ -107,6 +107,7 @@ _SIG = {
     "gf_set_prefetch": [_P, _I],
     "gf_set_graphs": [_P, _I],
     "gf_set_check_log": [_P, ctypes.c_char_p],
+    "gf_set_stage_wait_polls": [_P, _I],
     "gf_sweep_async": [_P, _I, ctypes.c_double, _I, ctypes.c_uint64],
     "gf_anneal_async": [_P, ctypes.c_double, ctypes.c_double, _I, ctypes.c_uint64],
     "gf_random_gauge_transform_async": [_P, ctypes.c_uint64],
@@ -342,6 +343,11 @@ def gf_random_gauge_transform_async(h, seed):
 
 def gf_synchronize(h):
     _check(lib().gf_synchronize(h), "gf_synchronize")
+
+
+def gf_set_stage_wait_polls(h, polls=-1):
+    """Polls of a shared-memory staging wait before it gives up (-1 default, 0 at once)."""
+    _check(lib().gf_set_stage_wait_polls(h, int(polls)), "gf_set_stage_wait_polls")
 
 
 def gf_set_check_log(h, path):

@@ -480,8 +480,13 @@ def test_prefetch_modes_agree(gf, synth, orc, gauge, prec, lpt):
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
     c = _prefetch_run(gf, U, gauge, prec, lpt, "l2", False)
     d = _prefetch_run(gf, U, gauge, prec, lpt, "smem", False)
+    # MAG's subgroup vector is quadratic in the links and its maximiser is
+    # ill-conditioned where that vector is small, so on this rough field FP32
+    # rounding differences between two compiled instances grow to ~2e-5 over
+    # the four sweeps (stale or misplaced staged data would give O(1) errors)
+    tol = 1e-4 if gauge == "mag" else 2e-5
     for x, y in zip(c[0], d[0]):
-        assert np.abs(x - y).max() <= 2e-5
+        assert np.abs(x - y).max() <= tol
     assert np.allclose(c[1], d[1], rtol=1e-6, atol=0)
 
 
@@ -597,6 +602,33 @@ def test_autotune_choice_carries_to_new_contexts(gf, synth, orc):
         assert gf.gf_get_links_per_thread(h) == best
         gf.gf_load_links(h, 0, np.ascontiguousarray(rough(synth, orc, (8, 8, 16, 8))))
         gf.gf_sweep(h, "or", 1.35, 2, observables=False)
+
+
+@pytest.mark.parametrize("lpt", [2, 4])
+def test_staging_wait_timeout_reported(gf, synth, orc, lpt):
+    """A staging wait that runs out (poll limit 0) makes the blocks drain
+    their copies and return; the host reads GF_ETIMEOUT, and the context
+    then sweeps normally (same result as a fresh context)."""
+    U = rough(synth, orc, DIMS)
+    with Ctx(gf, DIMS, "landau", "fp32") as h:
+        gf.gf_set_prefetch(h, "smem")
+        gf.gf_set_links_per_thread(h, lpt)
+        gf.gf_load_links(h, 0, U)
+        gf.gf_set_stage_wait_polls(h, 0)
+        with pytest.raises(gf.GFError) as e:
+            gf.gf_sweep(h, "or", 1.7, 1)
+        assert e.value.code == gf.GF_ETIMEOUT
+        gf.gf_set_stage_wait_polls(h, -1)
+        gf.gf_load_links(h, 0, U)
+        gf.gf_sweep(h, "or", 1.7, 3, observables=False)
+        A = store(gf, h, DIMS)
+    with Ctx(gf, DIMS, "landau", "fp32") as h:
+        gf.gf_set_prefetch(h, "smem")
+        gf.gf_set_links_per_thread(h, lpt)
+        gf.gf_load_links(h, 0, U)
+        gf.gf_sweep(h, "or", 1.7, 3, observables=False)
+        B = store(gf, h, DIMS)
+    assert np.array_equal(A, B)
 
 
 def test_prefetch_mode_invalid(gf):
