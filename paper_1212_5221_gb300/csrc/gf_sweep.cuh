@@ -32,15 +32,13 @@ struct SweepArgs {
                       // (2^24, about 2 s), 0 none (the wait runs out at once)
 };
 
-// Per-site FP64 observables from the slot matrices M (M = U_mu(x) for up
-// slots, U_mu(x-mu)^dag for down slots).  Each slot is taken as stored: the
-// two stored rows of its link, with the third rebuilt as conj(row0 x row1)
-// in FP64 (exactly what a later read of the links gives).  K(x) = sum of the
-// gathered slots, so theta_site = tr[Delta Delta^dag] with Delta the
-// traceless part of (K - K^dag)/(2i) (Landau/Coulomb), or sum over subgroups
-// |X_01|^2 with X = sum of the blocks' W s3 W^dag (MAG); F_site sums Re tr M
-// (Landau, Coulomb) or |M_kk|^2 (MAG).  Each lane adds its own slots in FP64;
-// an xor butterfly combines the lanes of the site.
+// Per-site FP64 observables of the MAG form from the slot matrices M
+// (M = U_mu(x) for up slots, U_mu(x-mu)^dag for down slots).  Each slot is
+// taken as stored: the two stored rows of its link, with the third rebuilt
+// as conj(row0 x row1) in FP64 (exactly what a later read of the links
+// gives).  theta_site = sum over subgroups |X_01|^2 with X = sum of the
+// blocks' W s3 W^dag; F_site = sum of |M_kk|^2.  Each lane adds its own slots
+// in FP64; an xor butterfly combines the lanes of the site.
 template <typename R>
 __device__ __forceinline__ void stored_slot(const mat3<R>& m, bool down, mat3<double>& d) {
   if (!down) {
@@ -63,87 +61,40 @@ __device__ __forceinline__ void stored_slot(const mat3<R>& m, bool down, mat3<do
   }
 }
 
-template <typename R, int GAUGE, int LPT>
-__device__ __forceinline__ void site_observables(const mat3<R> (&u)[LPT], const bool (&use)[LPT],
-                                                 const bool (&gather)[LPT], int lane, double& F,
-                                                 double& theta) {
+template <typename R, int LPT>
+__device__ __forceinline__ void site_observables_mag(const mat3<R> (&u)[LPT], const bool (&use)[LPT], int lane,
+                                                     double& F, double& theta) {
   constexpr int L = 8 / LPT;
   F = 0.0;
   theta = 0.0;
-  if (GAUGE == MAG) {
-    double xr[3] = {0, 0, 0}, xi[3] = {0, 0, 0};
+  double xr[3] = {0, 0, 0}, xi[3] = {0, 0, 0};
 #pragma unroll
-    for (int j = 0; j < LPT; ++j) {
-      if (!use[j]) continue;
-      mat3<double> m;
-      stored_slot(u[j], (LPT >= 2) ? (j & 1) : ((lane * LPT + j) & 1), m);
+  for (int j = 0; j < LPT; ++j) {
+    if (!use[j]) continue;
+    mat3<double> m;
+    stored_slot(u[j], (LPT >= 2) ? (j & 1) : ((lane * LPT + j) & 1), m);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) F += m.e[k][k].re * m.e[k][k].re + m.e[k][k].im * m.e[k][k].im;
+    for (int k = 0; k < 3; ++k) F += m.e[k][k].re * m.e[k][k].re + m.e[k][k].im * m.e[k][k].im;
 #pragma unroll
-      for (int sub = 0; sub < 3; ++sub) {
-        const int i = sub == 2 ? 1 : 0, i2 = sub == 0 ? 1 : 2;
-        const cx<double> A = m.e[i][i], B = m.e[i][i2], C = m.e[i2][i], D = m.e[i2][i2];
-        // A conj(C) - B conj(D)
-        xr[sub] += A.re * C.re + A.im * C.im - B.re * D.re - B.im * D.im;
-        xi[sub] += A.im * C.re - A.re * C.im - B.im * D.re + B.re * D.im;
-      }
+    for (int sub = 0; sub < 3; ++sub) {
+      const int i = sub == 2 ? 1 : 0, i2 = sub == 0 ? 1 : 2;
+      const cx<double> A = m.e[i][i], B = m.e[i][i2], C = m.e[i2][i], D = m.e[i2][i2];
+      // A conj(C) - B conj(D)
+      xr[sub] += A.re * C.re + A.im * C.im - B.re * D.re - B.im * D.im;
+      xi[sub] += A.im * C.re - A.re * C.im - B.im * D.re + B.re * D.im;
     }
-#pragma unroll
-    for (int o = 1; o < L; o <<= 1) {
-      F += __shfl_xor_sync(FULL, F, o);
-#pragma unroll
-      for (int sub = 0; sub < 3; ++sub) {
-        xr[sub] += __shfl_xor_sync(FULL, xr[sub], o);
-        xi[sub] += __shfl_xor_sync(FULL, xi[sub], o);
-      }
-    }
-#pragma unroll
-    for (int sub = 0; sub < 3; ++sub) theta += xr[sub] * xr[sub] + xi[sub] * xi[sub];
-  } else {
-    double kr[3][3], ki[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) kr[a][b] = ki[a][b] = 0.0;
-#pragma unroll
-    for (int j = 0; j < LPT; ++j) {
-      if (!(use[j] && gather[j])) continue;
-      mat3<double> m;
-      stored_slot(u[j], (LPT >= 2) ? (j & 1) : ((lane * LPT + j) & 1), m);
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          kr[a][b] += m.e[a][b].re;
-          ki[a][b] += m.e[a][b].im;
-        }
-    }
-#pragma unroll
-    for (int o = 1; o < L; o <<= 1)
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          kr[a][b] += __shfl_xor_sync(FULL, kr[a][b], o);
-          ki[a][b] += __shfl_xor_sync(FULL, ki[a][b], o);
-        }
-    F = kr[0][0] + kr[1][1] + kr[2][2];
-    double dr[3][3], di[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        dr[a][b] = 0.5 * (ki[a][b] + ki[b][a]);
-        di[a][b] = -0.5 * (kr[a][b] - kr[b][a]);
-      }
-    const double tr3 = (dr[0][0] + dr[1][1] + dr[2][2]) / 3.0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) dr[a][a] -= tr3;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) theta += dr[a][b] * dr[a][b] + di[a][b] * di[a][b];
   }
+#pragma unroll
+  for (int o = 1; o < L; o <<= 1) {
+    F += __shfl_xor_sync(FULL, F, o);
+#pragma unroll
+    for (int sub = 0; sub < 3; ++sub) {
+      xr[sub] += __shfl_xor_sync(FULL, xr[sub], o);
+      xi[sub] += __shfl_xor_sync(FULL, xi[sub], o);
+    }
+  }
+#pragma unroll
+  for (int sub = 0; sub < 3; ++sub) theta += xr[sub] * xr[sub] + xi[sub] * xi[sub];
 }
 
 // Element offset of (copy, parity, slot, chunk 0, site index).
@@ -382,21 +333,19 @@ __device__ __forceinline__ void load_slot(const float4* stage, const Geom& G, ui
 }
 
 // ---------------------------------------------------------------------------
-// One half-sweep (Alg. 1 for one sublattice).  L = 8/LPT lanes share a site;
-// lane l holds slots l*LPT .. l*LPT+LPT-1 of the site's eight links, slot
-// k = 2 mu + d: d = 0 is U_mu(x), d = 1 is U_mu(x - mu)^dagger, so that every
-// slot's K contribution (Eq. Kx) is its (i,j) block and every update is a
-// left multiplication by g.  Per subgroup, the lanes' partial quaternions
-// (Landau/Coulomb) or Pauli vectors (MAG) are summed with an xor butterfly of
-// warp shuffles, which gives bit-identical sums in all lanes, so all lanes
-// compute the same g (Step 1) and apply it to their own slots (Step 2).
-// Coulomb: slot 0 holds the accumulated g(x) of the time-slice sweep (updated,
-// not gathered) and slot 1 is idle; the temporal links are not touched.
-// The grid is persistent over tiles of BLOCK/L sites; each block prefetches
-// its next tile into L2 while it works on the current one.
-template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
-__device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy, uint32_t sp, bool valid,
-                                           int lane, const float4* stage, uint32_t sp0) {
+// One half-sweep (Alg. 1 for one sublattice), MAG form.  L = 8/LPT lanes
+// share a site; lane l holds slots l*LPT .. l*LPT+LPT-1 of the site's eight
+// links, slot k = 2 mu + d: d = 0 is U_mu(x), d = 1 is U_mu(x - mu)^dagger,
+// so that every update is a left multiplication by g.  MAG's subgroup vector
+// is quadratic in the links, so each subgroup is applied to every slot
+// before the next subgroup's vector is formed.  Per subgroup, the lanes'
+// partial Pauli vectors are summed with an xor butterfly of warp shuffles,
+// which gives bit-identical sums in all lanes, so all lanes compute the same
+// g (Step 1) and apply it to their own slots (Step 2).  The grid is
+// persistent over tiles of BLOCK/L sites.
+template <typename R, int ALGO, int LPT, bool OBS>
+__device__ __forceinline__ void sweep_site_mag(const SweepArgs<R>& a, uint32_t copy, uint32_t sp, bool valid,
+                                               int lane, const float4* stage, uint32_t sp0) {
   constexpr uint32_t TILE = BLOCK / (8 / LPT);
   constexpr int NC = store_traits<R>::NC;
   constexpr int L = 8 / LPT;
@@ -416,15 +365,13 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
   const bool NORM = (sizeof(R) == 4 || ALGO != ALG_OR) && (!OBS || a.update);
   mat3<R> u[LPT];
   size_t off[LPT];
-  bool use[LPT], gather[LPT];
+  bool use[LPT];
 #pragma unroll
   for (int j = 0; j < LPT; ++j) {
     const int k = lane * LPT + j;
     const int mu = k >> 1;
     const bool down = (LPT >= 2) ? (j & 1) : (k & 1);
-    gather[j] = !(GAUGE == COULOMB && mu == 0);
-    use[j] = valid && !(GAUGE == COULOMB && mu == 0 && down);
-    const int slot = (GAUGE == COULOMB && mu == 0) ? 4 : mu;
+    use[j] = valid;
     uint32_t ssp = sp;
     int par = a.parity;
     if (down) {
@@ -435,7 +382,7 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
       ssp = (cm > 0 ? s - st : s + (uint32_t)(nm - 1) * st) >> 1;
       par ^= 1;
     }
-    off[j] = link_off(copy, par, slot, a.NS, NC, Vh, ssp);
+    off[j] = link_off(copy, par, mu, a.NS, NC, Vh, ssp);
     if (use[j]) {
       load_slot<R, TILE>(stage, G, sp0, k, ssp, a.links + off[j], Vh, u[j]);
       if (NORM) reproject_rows(u[j]);
@@ -448,7 +395,7 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
 
   // mixed precision: the accumulated gauge transformation of this site (the
   // FP32 working copy only, so FP64 kernels carry no code for it)
-  constexpr bool CAN_ACC = sizeof(R) == 4 && GAUGE != COULOMB;
+  constexpr bool CAN_ACC = sizeof(R) == 4;
   const bool acc = CAN_ACC && a.acc;
   mat3<R> gacc;
   size_t acc_off = 0;
@@ -466,9 +413,9 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
 
   Rng rng{a.k0, a.k1, s, a.sweep, a.copy0 + copy};
 
-  if (OBS && a.obs == 1) {  // theta of the current links at this site (K as gathered)
+  if (OBS && a.obs == 1) {  // theta of the current links at this site
     double F, th;
-    site_observables<R, GAUGE, LPT>(u, use, gather, lane, F, th);
+    site_observables_mag<R, LPT>(u, use, lane, F, th);
     if (valid && lane == 0) a.obs_site[(size_t)copy * G.V + s] = make_double2(0.0, th);
   }
   if (OBS && !a.update) return;
@@ -477,66 +424,35 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
   for (int sub = 0; sub < 3; ++sub) {
     const int i = sub == 2 ? 1 : 0;
     const int j2 = sub == 0 ? 1 : 2;
+    // x = Pauli vector of sum W s3 W^dag over the slots' (i,j) blocks
+    R x1 = 0, x2 = 0, x3 = 0;
+#pragma unroll
+    for (int j = 0; j < LPT; ++j) {
+      if (!use[j]) continue;
+      cx<R> A = u[j].e[i][i], B = u[j].e[i][j2], C = u[j].e[j2][i], D = u[j].e[j2][j2];
+      cx<R> x01 = cmul2c(A, C, cx<R>{-B.re, -B.im}, D);  // A conj(C) - B conj(D)
+      x1 += x01.re;
+      x2 -= x01.im;
+      x3 += R(0.5) * ((A.re * A.re + A.im * A.im) - (B.re * B.re + B.im * B.im) -
+                      (C.re * C.re + C.im * C.im) + (D.re * D.re + D.im * D.im));
+    }
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) {
+      x1 += __shfl_xor_sync(FULL, x1, o);
+      x2 += __shfl_xor_sync(FULL, x2, o);
+      x3 += __shfl_xor_sync(FULL, x3, o);
+    }
+    R r;
+    quat<R> m = mag_max(x1, x2, x3, r);
     quat<R> g;
-    if (GAUGE == MAG) {
-      // x = Pauli vector of sum W s3 W^dag over the slots' (i,j) blocks
-      R x1 = 0, x2 = 0, x3 = 0;
-#pragma unroll
-      for (int j = 0; j < LPT; ++j) {
-        if (!use[j]) continue;
-        cx<R> A = u[j].e[i][i], B = u[j].e[i][j2], C = u[j].e[j2][i], D = u[j].e[j2][j2];
-        cx<R> x01 = cmul2c(A, C, cx<R>{-B.re, -B.im}, D);  // A conj(C) - B conj(D)
-        x1 += x01.re;
-        x2 -= x01.im;
-        x3 += R(0.5) * ((A.re * A.re + A.im * A.im) - (B.re * B.re + B.im * B.im) -
-                        (C.re * C.re + C.im * C.im) + (D.re * D.re + D.im * D.im));
-      }
-#pragma unroll
-      for (int o = 1; o < L; o <<= 1) {
-        x1 += __shfl_xor_sync(FULL, x1, o);
-        x2 += __shfl_xor_sync(FULL, x2, o);
-        x3 += __shfl_xor_sync(FULL, x3, o);
-      }
-      R r;
-      quat<R> m = mag_max(x1, x2, x3, r);
-      if (ALGO == ALG_OR) g = rule_or(m, a.param);
-      else if (ALGO == ALG_MICRO) g = mag_micro(x1, x2, x3, r);
-      else if (ALGO == ALG_SR) {
-        double ua, ub;
-        rng.draw2(TAG_SR, (uint32_t)sub, 0, ua, ub);
-        g = ((R)ua < a.param) ? mag_micro(x1, x2, x3, r) : rule_or(m, R(1));
-      } else {
-        g = rule_sa_mag(m, r, a.param, rng, (uint32_t)sub);
-      }
+    if (ALGO == ALG_OR) g = rule_or(m, a.param);
+    else if (ALGO == ALG_MICRO) g = mag_micro(x1, x2, x3, r);
+    else if (ALGO == ALG_SR) {
+      double ua, ub;
+      rng.draw2(TAG_SR, (uint32_t)sub, 0, ua, ub);
+      g = ((R)ua < a.param) ? mag_micro(x1, x2, x3, r) : rule_or(m, R(1));
     } else {
-      // quaternion of the (i,j) block of K (getSubgroupQuaternion, App. A)
-      R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-#pragma unroll
-      for (int j = 0; j < LPT; ++j) {
-        if (!(use[j] && gather[j])) continue;
-        cx<R> W00 = u[j].e[i][i], W01 = u[j].e[i][j2], W10 = u[j].e[j2][i], W11 = u[j].e[j2][j2];
-        a0 += W00.re + W11.re;
-        a1 += W01.im + W10.im;
-        a2 += W01.re - W10.re;
-        a3 += W00.im - W11.im;
-      }
-#pragma unroll
-      for (int o = 1; o < L; o <<= 1) {
-        a0 += __shfl_xor_sync(FULL, a0, o);
-        a1 += __shfl_xor_sync(FULL, a1, o);
-        a2 += __shfl_xor_sync(FULL, a2, o);
-        a3 += __shfl_xor_sync(FULL, a3, o);
-      }
-      quat<R> m{a0, -a1, -a2, -a3};  // maximiser of Re tr(g W)
-      if (ALGO == ALG_OR) g = rule_or(m, a.param);
-      else if (ALGO == ALG_MICRO) g = rule_micro(m);
-      else if (ALGO == ALG_SR) {
-        double ua, ub;
-        rng.draw2(TAG_SR, (uint32_t)sub, 0, ua, ub);
-        g = ((R)ua < a.param) ? rule_micro(m) : rule_or(m, R(1));
-      } else {
-        g = rule_sa_landau(m, a.param, rng, (uint32_t)sub);
-      }
+      g = rule_sa_mag(m, r, a.param, rng, (uint32_t)sub);
     }
 #pragma unroll
     for (int j = 0; j < LPT; ++j) left_subgroup_mult(u[j], i, j2, g);
@@ -545,7 +461,7 @@ __device__ __forceinline__ void sweep_site(const SweepArgs<R>& a, uint32_t copy,
   if (use_acc) store_rows(a.links + acc_off, Vh, gacc);
   if (OBS && a.obs == 2) {  // F (every link is written once in a half-sweep) and theta after the update
     double F, th;
-    site_observables<R, GAUGE, LPT>(u, use, gather, lane, F, th);
+    site_observables_mag<R, LPT>(u, use, lane, F, th);
     if (valid && lane == 0) a.obs_site[(size_t)copy * G.V + s] = make_double2(F, th);
   }
 
@@ -882,7 +798,7 @@ template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
 __device__ __forceinline__ void site_dispatch(const SweepArgs<R>& a, uint32_t copy, uint32_t sp, bool valid, int lane,
                                               const float4* stage, uint32_t sp0) {
   if constexpr (GAUGE == MAG)
-    sweep_site<R, GAUGE, ALGO, LPT, OBS>(a, copy, sp, valid, lane, stage, sp0);
+    sweep_site_mag<R, ALGO, LPT, OBS>(a, copy, sp, valid, lane, stage, sp0);
   else
     sweep_site_k<R, GAUGE, ALGO, LPT, OBS>(a, copy, sp, valid, lane, stage, sp0);
 }
