@@ -72,11 +72,6 @@ class Arena {
   }
   size_t used() const { return used_; }
   size_t size() const { return size_; }
-  size_t largest_free() const {
-    size_t m = 0;
-    for (auto& f : free_) m = std::max(m, f.second);
-    return m;
-  }
 
  private:
   size_t size_, used_ = 0;
@@ -121,7 +116,7 @@ int sfail(int code, const char* msg) {
 }
 
 // Run one admitted job on its own context carved from the arena block.
-void run_job(gf_server* S, const gf_job& J, char* mem, size_t bytes, gf_job_result& R) {
+void run_job(const gf_job& J, char* mem, size_t bytes, gf_job_result& R) {
   nvtxRangePushA("server job");
   gf_ctx* c = nullptr;
   int r = gf_create_ext(J.dims, 1, J.gauge, J.prec, nullptr, mem, bytes, &c);
@@ -189,7 +184,7 @@ void worker_main(gf_server* S) {
       std::this_thread::sleep_for(std::chrono::duration<double>(S->mock_seconds_per_gb * P.bytes / 1e9));
       R.status = GF_OK;
     } else {
-      run_job(S, P.job, S->base + off, P.bytes, R);
+      run_job(P.job, S->base + off, P.bytes, R);
     }
     R.t_done = S->now();
     {
