@@ -25,7 +25,8 @@
  *    array of n_copies doubles (per-slice outputs: n_copies*Nt doubles).
  *    Results are FP64 whatever the storage precision.
  *  - Work is issued on the context's CUDA stream; every call returns after
- *    its work on that stream has completed.
+ *    its work on that stream has completed, except the *_async calls, which
+ *    return once the work is enqueued (gf_synchronize waits for it).
  *  - A context must not be used from two threads at the same time.
  */
 #ifndef GF_H
@@ -252,19 +253,25 @@ int gf_autotune(gf_ctx* ctx, gf_algo algo, int* best_lpt, double* ms_per_sweep_b
  * later start from it (a job server tunes each class once). */
 
 /* Drive the sweeps to theta < theta_target (the while-loop of Alg. 1).
- * theta is evaluated every check_interval sweeps; a unit (a copy, or for
- * Coulomb a copy's time-slice) stops as soon as its theta is below target.
- * FP32 storage is re-unitarised every reunit_interval sweeps (Sec. 4.5).
+ * theta is evaluated after check_interval sweeps; once two evaluations show
+ * theta falling geometrically, the next one is scheduled at 0.7 times the
+ * predicted crossing of the current threshold (between 1 and 10
+ * check_interval sweeps).  A unit (a copy, or for Coulomb a copy's
+ * time-slice) stops as soon as its theta is below target.  The odd half of
+ * the sweep before a check also sums F and theta (gf_set_fused_observables).
+ * Storage is re-unitarised every reunit_interval sweeps (Sec. 4.5).
  * GF_MIXED runs FP32 sweeps until every active unit has theta < switch_theta
- * (or theta has not improved for 25 checks: the FP32 rounding floor), then
- * promotes to the FP64 master for the final sweeps; a unit counts as
- * converged only on FP64 links. */
+ * (or, once theta is below max(100 switch_theta, 1e-9), it has not improved
+ * for 25 check intervals: the FP32 rounding floor), then continues on the
+ * FP64 master for the final sweeps; a unit counts as converged only on FP64
+ * links.  Blocks of plain sweeps are replayed as CUDA graphs
+ * (gf_set_graphs). */
 typedef struct {
   gf_algo algo;          /* GF_OR or GF_RELAX */
   double param;          /* omega */
   double theta_target;   /* e.g. 1e-12 */
   int max_sweeps;        /* per run; GF_ENOTCONV beyond */
-  int check_interval;    /* sweeps between theta evaluations, >= 1 */
+  int check_interval;    /* sweeps before the first theta evaluations (the base interval), >= 1 */
   int reunit_interval;   /* every this many sweeps re-unitarise the links (GF_FP32, GF_FP64, and
                             GF_MIXED's FP64 stage) or apply the accumulated transformation to the
                             FP64 master (GF_MIXED's FP32 stage); 0 = never */
