@@ -389,7 +389,7 @@ typedef struct {
 
 typedef struct {
   uint64_t tag;
-  int status;            /* GF_OK, GF_ENOTCONV, or an error code */
+  int status;            /* GF_OK, GF_ENOTCONV, GF_ECANCELED (gf_server_cancel), or an error code */
   double F, theta;
   int sweeps, sweeps_fp32, sweeps_fp64;
   uint64_t site_updates;
