@@ -14,8 +14,7 @@
  *   - local relaxation: Sec. 2.2 (Eqs. landau_loc, Kx, localsolution), with
  *     the three Cabibbo-Marinari SU(2) subgroups;
  *   - MAG local maximum: Sec. 2.2.2 (Eqs. up, upMatrix);
- *   - overrelaxation / microcanonical / stochastic relaxation: Secs. 2.2.3-5
- *     and the OrUpdate figure of App. A;
+ *   - overrelaxation / microcanonical / stochastic relaxation: Secs. 2.2.3-5;
  *   - simulated annealing with heatbath + 3 microcanonical steps: Sec. 2.3;
  *   - the checkerboard sweep: Sec. 2.4, Alg. 1;
  *   - unitarity measure: Sec. 4.5.
@@ -480,10 +479,10 @@ void or_unitarity(const int dims[4], const double* U, double* mean,
 /* ------------------------------------------------------------------------ */
 /* Step 1: the local SU(2) update for one subgroup. */
 
-/* The maximiser direction for Landau/Coulomb: the quaternion a extracted
- * from the (i,j) block W of K as in the getSubgroupQuaternion figure of
- * App. A, a = (Re W00 + Re W11, Im W01 + Im W10, Re W01 - Re W10,
- * Im W00 - Im W11).  Re tr(g W) = g0 a0 - g.a, so the maximiser is the
+/* The maximiser direction for Landau/Coulomb.  For the Cayley-Klein g and
+ * the (i,j) block W of K, expanding the trace gives Re tr(g W) = g0 a0 - g.a
+ * with a = (Re W00 + Re W11, Im W01 + Im W10, Re W01 - Re W10,
+ * Im W00 - Im W11) (the same four sums as App. A), so the maximiser is the
  * conjugate (a0, -a1, -a2, -a3) normalised (Eq. localsolution for SU(2)). */
 static void landau_maximiser(const su3* K, int i, int j, double m[4]) {
   cplx W00 = K->m[i][i], W01 = K->m[i][j], W10 = K->m[j][i], W11 = K->m[j][j];
@@ -522,24 +521,27 @@ static void mag_maximiser(const double x[3], double m[4]) {
   m[2] = v2 / n;
 }
 
-/* Overrelaxation, as in the OrUpdate figure of App. A: with a0^2 and
- * |a|^2 = a1^2 + a2^2 + a3^2, b = (w a0^2 + |a|^2)/(a0^2 + |a|^2),
- * c = 1/sqrt(a0^2 + b^2 |a|^2), g = (c a0, b c a1, b c a2, b c a3).  A
- * first-order form of g -> g^w (Sec. 2.2.3); w = 1 is plain relaxation.
- * READING: a zero quaternion gives the identity. */
+/* Overrelaxation (Sec. 2.2.3): the relaxation update g is replaced by its
+ * power g^w, taken to first order in the rotation angle.  With q = m/|m| =
+ * (q0, v) the unit maximiser, the vector part is stretched by
+ * s = 1 + (w - 1) q0^2 and the result normalised, g = (q0, s v)/|(q0, s v)|:
+ * for the small rotations near convergence q0 -> 1 and s -> w, so the angle
+ * grows by w (g^w to first order); for a rotation by pi (q0 = 0) s = 1.
+ * READING: Sec. 2.2.3 does not write the first-order form out; App. A's update
+ * uses this stretch factor.  w = 1 is plain relaxation; a zero quaternion
+ * gives the identity. */
 static void or_update(const double m[4], double omega, double g[4]) {
-  double a0sq = m[0] * m[0];
-  double aisq = m[1] * m[1] + m[2] * m[2] + m[3] * m[3];
-  if (a0sq + aisq == 0) {
+  double nm = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2] + m[3] * m[3]);
+  if (nm == 0) {
     g[0] = 1; g[1] = g[2] = g[3] = 0;
     return;
   }
-  double b = (omega * a0sq + aisq) / (a0sq + aisq);
-  double c = 1.0 / sqrt(a0sq + b * b * aisq);
-  g[0] = c * m[0];
-  g[1] = b * c * m[1];
-  g[2] = b * c * m[2];
-  g[3] = b * c * m[3];
+  double q[4];
+  for (int k = 0; k < 4; ++k) q[k] = m[k] / nm;
+  double s = 1.0 + (omega - 1.0) * q[0] * q[0];
+  double h[4] = {q[0], s * q[1], s * q[2], s * q[3]};
+  double nh = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2] + h[3] * h[3]);
+  for (int k = 0; k < 4; ++k) g[k] = h[k] / nh;
 }
 
 /* Microcanonical step (Sec. 2.2.4): the square of the normalised maximiser,

@@ -362,7 +362,7 @@ def test_mag_maximiser_closed_form(orc):
 
 
 # --------------------------------------------------------------------------
-# Update rules (OrUpdate figure, microcanonical step)
+# Update rules (overrelaxation, microcanonical step)
 
 
 def test_or_rule_values(orc):
