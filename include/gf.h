@@ -58,8 +58,8 @@ typedef enum { GF_LANDAU = 0, GF_COULOMB = 1, GF_MAG = 2 } gf_gauge;
 typedef enum { GF_FP64 = 0, GF_FP32 = 1, GF_MIXED = 2 } gf_precision;
 
 /* Local update (Step 1 of Alg. 1): relaxation (Eq. localsolution per SU(2)
- * subgroup), overrelaxation g -> g^omega to first order (Sec. 2.2.3, the
- * OrUpdate figure of App. A), microcanonical g -> g^2 (Sec. 2.2.4),
+ * subgroup), overrelaxation g -> g^omega to first order (Sec. 2.2.3, in
+ * the form of App. A), microcanonical g -> g^2 (Sec. 2.2.4),
  * stochastic relaxation (Sec. 2.2.5), simulated-annealing heat bath
  * (Sec. 2.3). */
 typedef enum { GF_RELAX = 0, GF_OR = 1, GF_MICRO = 2, GF_SR = 3, GF_SA = 4 } gf_algo;
@@ -248,9 +248,10 @@ int gf_get_links_per_thread(gf_ctx* ctx, int* lpt);
  * links, restore them, and keep the fastest for (storage precision, algo).
  * A later gf_set_prefetch replaces the tuned tile fetch. */
 int gf_autotune(gf_ctx* ctx, gf_algo algo, int* best_lpt, double* ms_per_sweep_best);
-/* The choice is also kept for the process, per (gauge, storage precision,
- * algorithm, lattice class = floor(log2(sites x copies))): contexts created
- * later start from it (a job server tunes each class once). */
+/* The choice is also kept for the process, per (CUDA device current at
+ * creation, gauge, storage precision, algorithm, lattice class =
+ * floor(log2(sites x copies))): contexts created later on the same device
+ * start from it (a job server tunes each class once). */
 
 /* Drive the sweeps to theta < theta_target (the while-loop of Alg. 1).
  * theta is evaluated after check_interval sweeps; once two evaluations show
@@ -355,7 +356,9 @@ int gf_launch_count(gf_ctx* ctx, uint64_t* n);
  * library routine).  Every call shares that array and it keeps the last
  * call's contents, so calls that overlap on the GPU race: serialise them.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any CUDA stream capture.
+ * device current), so it should come before any CUDA stream capture starts.
+ * Every call, the first included, ends by copying its results to the host
+ * and synchronising `stream`: it returns only once they are there.
  * Returns GF_EINVAL for sizes beyond the maximum or misaligned input. */
 #define GF_NOALLOC_MAX_NT 1024
 int gf_functional_theta_noalloc(const int dims[4], gf_gauge gauge, const double* device_links, void* stream,

@@ -57,12 +57,21 @@ struct Range {
 };
 
 // Launch parameters chosen by gf_autotune, kept for the process per
-// (gauge, storage is FP64, algorithm, floor(log2(sites x copies))).
+// (device, gauge, storage is FP64, algorithm, floor(log2(sites x copies))).
 struct Tuned {
   int lpt, pmode;
 };
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, Tuned> g_tuned;
+std::map<std::tuple<int, int, int, int, int>, Tuned> g_tuned;
+
+int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  return dev;
+}
 
 int volume_class(uint64_t v) {
   int k = 0;
@@ -142,6 +151,7 @@ void gfk::set_last_error(const char* msg) { g_last_error = msg; }
 struct gf_ctx {
   int dims[4];
   int ncopies, gauge, prec;
+  int device = 0;  // the CUDA device current when the context was created
   int NS32, NS64;  // slots per site in the FP32 / FP64 arrays
   Geom G;
   Layout layout;
@@ -184,7 +194,7 @@ struct gf_ctx {
   // their launch arguments depend on
   bool use_graphs = true;
   bool warm = false;  // sweep kernels launched once outside capture (one-time setup done)
-  using GraphKey = std::tuple<int, int, int, int, int, int, uint64_t, uint32_t>;
+  using GraphKey = std::tuple<int, int, int, int, int, int, uint64_t, uint32_t, int>;
   std::map<GraphKey, cudaGraphExec_t> graphs;
   FILE* check_log = nullptr;  // JSON lines, one per convergence check
 
@@ -349,8 +359,9 @@ int plain_sweeps(gf_ctx* c, int kalgo, int api_algo, double param, int n) {
     const bool acc = c->prec == GF_MIXED && !c->fp64 && c->gauge != GF_COULOMB;
     uint64_t pbits;
     memcpy(&pbits, &param, sizeof pbits);
-    const gf_ctx::GraphKey key{c->fp64, lpt, pm >= 0 ? pm : c->prefetch, kalgo, c->all_active, acc, pbits,
-                               c->copy_base};
+    const int mode = pm >= 0 ? pm : c->prefetch;
+    const gf_ctx::GraphKey key{c->fp64, lpt, mode, kalgo, c->all_active, acc, pbits, c->copy_base,
+                               c->stage_wait_polls};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
       const uint64_t idx = c->sweep_index, nl = c->launch_count;
@@ -376,6 +387,8 @@ int plain_sweeps(gf_ctx* c, int kalgo, int api_algo, double param, int n) {
       it = c->graphs.emplace(key, x).first;
     }
     GF_CUDA(cudaGraphLaunch(it->second, c->st));
+    // a replayed staged sweep can record a staging timeout like a direct launch
+    if (!c->fp64 && mode == GF_PREFETCH_SMEM) c->err_pending = true;
     c->sweep_index += GRAPH_SWEEPS;
     c->launch_count += 2 * GRAPH_SWEEPS;
     if (c->prec == GF_MIXED && !c->fp64) c->dirty = true;
@@ -524,6 +537,7 @@ int create_impl(const int dims[4], int ncopies, int gauge, int prec, void* strea
   c->ncopies = ncopies;
   c->gauge = gauge;
   c->prec = prec;
+  c->device = current_device();
   c->NS32 = (gauge == GF_COULOMB || prec == GF_MIXED) ? 5 : 4;
   c->NS64 = gauge == GF_COULOMB ? 5 : 4;
   c->G = make_geom(dims);
@@ -587,7 +601,7 @@ int create_impl(const int dims[4], int ncopies, int gauge, int prec, void* strea
     const int vc = volume_class((uint64_t)c->G.V * (uint64_t)c->ncopies);
     for (int f64 = 0; f64 < 2; ++f64)
       for (int a = 0; a < 5; ++a) {
-        auto it = g_tuned.find(std::make_tuple(c->gauge, f64, a, vc));
+        auto it = g_tuned.find(std::make_tuple(c->device, c->gauge, f64, a, vc));
         if (it != g_tuned.end()) {
           c->lpt[f64][a] = it->second.lpt;
           c->pmode[f64][a] = it->second.pmode + 1;
@@ -1132,7 +1146,7 @@ int gf_autotune(gf_ctx* c, gf_algo algo, int* best_lpt, double* ms_best) {
   c->pmode[c->fp64][algo] = best_mode + 1;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tuned[std::make_tuple(c->gauge, (int)c->fp64, (int)algo,
+    g_tuned[std::make_tuple(c->device, c->gauge, (int)c->fp64, (int)algo,
                             volume_class((uint64_t)c->G.V * (uint64_t)c->ncopies))] = Tuned{best, best_mode};
   }
   if (best_lpt) *best_lpt = best;

@@ -244,13 +244,14 @@ __device__ __forceinline__ quat<R> qidentity() {
   return {R(1), R(0), R(0), R(0)};
 }
 
-// Overrelaxation on the maximiser direction m (OrUpdate figure, App. A):
-// b = (w a0^2 + |a|^2)/(a0^2 + |a|^2), c = 1/sqrt(a0^2 + b^2 |a|^2),
-// g = (c a0, b c a).  w = 1 is relaxation.  A zero m gives the identity.
+// Overrelaxation (Sec. 2.2.3): g^w to first order in the rotation angle.  On
+// the maximiser direction m = (a0, a), the vector part is stretched by
+// b = 1 + (w - 1) a0^2/|m|^2 and the result normalised; w = 1 is relaxation,
+// a zero m gives the identity.
 template <typename R>
 __device__ __forceinline__ quat<R> rule_or(quat<R> m, R omega) {
-  // on the normalised quaternion (a0^2 + |a|^2 = 1), so that two reciprocal
-  // square roots replace the division and the square root
+  // x0, xi: the squared parts of the normalised quaternion, so that two
+  // reciprocal square roots replace the division and the square root
   R a0 = m.q0 * m.q0;
   R ai = m.q1 * m.q1 + m.q2 * m.q2 + m.q3 * m.q3;
   R den = a0 + ai;

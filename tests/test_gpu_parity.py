@@ -631,6 +631,40 @@ def test_staging_wait_timeout_reported(gf, synth, orc, lpt):
     assert np.array_equal(A, B)
 
 
+def test_staging_wait_timeout_in_graph_replay(gf, synth, orc):
+    """Blocks of 16 sweeps replay a captured graph: a staging wait that runs
+    out inside a replay is reported at the next synchronisation, on every
+    replay (not only the one that captured), and a changed poll limit gives a
+    new graph (the old one keeps its own limit)."""
+    U = rough(synth, orc, DIMS)
+    with Ctx(gf, DIMS, "landau", "fp32") as h:
+        gf.gf_set_prefetch(h, "smem")
+        gf.gf_set_links_per_thread(h, 4)
+        gf.gf_load_links(h, 0, U)
+        gf.gf_sweep_async(h, "or", 1.7, 1)  # warm: later blocks of 16 replay graphs
+        gf.gf_synchronize(h)
+        gf.gf_set_stage_wait_polls(h, 0)
+        for _ in range(2):  # the first call captures, the second only replays
+            gf.gf_sweep_async(h, "or", 1.7, 16)
+            with pytest.raises(gf.GFError) as e:
+                gf.gf_synchronize(h)
+            assert e.value.code == gf.GF_ETIMEOUT
+        gf.gf_set_stage_wait_polls(h, -1)
+        gf.gf_load_links(h, 0, U)
+        gf.gf_sweep_async(h, "or", 1.7, 1)
+        gf.gf_sweep_async(h, "or", 1.7, 32)
+        gf.gf_synchronize(h)
+        A = store(gf, h, DIMS)
+    with Ctx(gf, DIMS, "landau", "fp32") as h:
+        gf.gf_set_prefetch(h, "smem")
+        gf.gf_set_links_per_thread(h, 4)
+        gf.gf_set_graphs(h, False)
+        gf.gf_load_links(h, 0, U)
+        gf.gf_sweep(h, "or", 1.7, 33, observables=False)
+        B = store(gf, h, DIMS)
+    assert np.array_equal(A, B)
+
+
 def test_prefetch_mode_invalid(gf):
     with Ctx(gf, (4, 4, 4, 4), "landau", "fp32") as h:
         for mode in (-1, 3):
