@@ -135,16 +135,35 @@ int gf_random_gauge_transform(gf_ctx* ctx, uint64_t seed);
  * [1,2] for GF_OR (GF_RELAX ignores it and uses 1), the probability p in
  * [0,1] for GF_SR, the temperature T > 0 for GF_SA, unused for GF_MICRO.
  * GF_SA: every sweep is one heat-bath sweep followed by three microcanonical
- * sweeps (Sec. 2.3).  Random draws are keyed by (seed, site, sweep index,
- * copy); the context's sweep index advances by one per sweep (four per SA
- * sweep).  F and theta (may be NULL) receive the exact values after the
- * sweeps, per copy. */
+ * sweeps (Sec. 2.3; the count is set by gf_set_sa_micro).  Random draws are
+ * keyed by (seed, site, sweep index, copy); the context's sweep index
+ * advances by one per sweep (1 + the microcanonical count per SA sweep).  F
+ * and theta (may be NULL) receive the exact values after the sweeps, per
+ * copy. */
 int gf_sweep(gf_ctx* ctx, gf_algo algo, double param, int n_sweeps, uint64_t seed, double* F,
              double* theta);
 
 /* Simulated annealing: n_steps heat-bath sweeps with T falling linearly from
  * T0 to T1, each followed by three microcanonical sweeps (Sec. 2.3). */
 int gf_anneal(gf_ctx* ctx, double T0, double T1, int n_steps, uint64_t seed, double* F, double* theta);
+
+/* Microcanonical sweeps after every heat-bath sweep of GF_SA, gf_anneal and
+ * gf_protocol: 3 by default, as in Sec. 2.3 ("three microcanonical steps
+ * after each change in temperature"); 0 runs the heat bath alone (the form
+ * its per-sweep parity is checked in).  GF_EINVAL outside [0, 64]. */
+int gf_set_sa_micro(gf_ctx* ctx, int n_micro);
+
+/* Diagnostic record of the Landau/Coulomb heat bath's accept/reject
+ * decisions (Kennedy-Pendleton, Sec. 2.3): while set, every heat-bath
+ * half-sweep writes, for each updated site and subgroup, the number of
+ * trials it took (1..64; 0 when none was accepted and the relaxation value
+ * was kept; always 1 for MAG, whose sampler has no rejection step).
+ *   device_counts  int32 device memory of n_copies*V*3 entries, layout
+ *                  [copy][lexicographic site][subgroup]; owned by the caller,
+ *                  who keeps it alive while it is set; NULL turns the record
+ *                  off.  Entries of sites not updated are left as they were.
+ * GF_EINVAL if the pointer is not 4-byte aligned. */
+int gf_set_sa_trace(gf_ctx* ctx, int* device_counts);
 
 /* Re-unitarise every stored matrix in FP64: normalise row 0, Gram-Schmidt
  * row 1, normalise; row 2 = conj(row0 x row1) (Sec. 4.5, reprojection). */

@@ -84,6 +84,9 @@ def _load():
                                            ctypes.c_int, _D, _U32, _U64, _U32]),
         "or_sweep": (None, [_PI, _V, ctypes.c_int, ctypes.c_int, _D, ctypes.c_int, _U32, _U64,
                             _U32, _V]),
+        "or_sweep_trace": (None, [_PI, _V, ctypes.c_int, ctypes.c_int, _D, ctypes.c_int, _U32, _U64,
+                                  _U32, _V, _V, _V]),
+        "or_sa_update": (ctypes.c_int, [ctypes.c_int, _PD, _D, _U64, _U32, _U32, _U32, _U32, _PD]),
         "or_anneal": (None, [_PI, _V, ctypes.c_int, _D, _D, ctypes.c_int, _U32, _U64, _U32]),
         "or_step_quaternion": (None, [_PD, ctypes.c_int, _D, _PD]),
         "or_haar_field": (None, [_U64, _U32, ctypes.c_long, _U32, _V]),
@@ -214,6 +217,34 @@ def sweep(U, gauge, algo, param=1.0, n=1, sweep0=0, seed=0, copy=0, slice_active
             raise ValueError("slice_active needs one flag per time-slice")
     _load().or_sweep(_dims(U), U.ctypes.data, _gauge(gauge), _algo(algo), param, n, sweep0,
                      seed & (2**64 - 1), copy, None if act is None else act.ctypes.data)
+
+
+def sweep_trace(U, gauge, algo, param=1.0, n=1, sweep0=0, seed=0, copy=0, slice_active=None):
+    """As sweep(); also returns, for the last sweep, the heat-bath trial count
+    and decision margin of every (site, subgroup): arrays of shape (V, 3)
+    (1 and inf where no accept/reject decision was taken)."""
+    act = None
+    if slice_active is not None:
+        act = np.ascontiguousarray(slice_active, dtype=np.int32)
+        if act.shape != (U.shape[0],):
+            raise ValueError("slice_active needs one flag per time-slice")
+    V = int(np.prod(U.shape[:4]))
+    trials = np.zeros((V, 3), np.int32)
+    margin = np.zeros((V, 3), np.float64)
+    _load().or_sweep_trace(_dims(U), U.ctypes.data, _gauge(gauge), _algo(algo), param, n, sweep0,
+                           seed & (2**64 - 1), copy, None if act is None else act.ctypes.data,
+                           trials.ctypes.data, margin.ctypes.data)
+    return trials, margin
+
+
+def sa_update(gauge, v, T, seed, site, sweep=0, sub=0, copy=0):
+    """The full heat-bath update of one subgroup: from the maximiser direction
+    m (Landau/Coulomb, 4 entries) or the Pauli vector x (MAG, 3 entries).
+    Returns (g, trials)."""
+    vv = (_D * 4)(*([float(a) for a in v] + [0.0] * (4 - len(v))))
+    g = (_D * 4)()
+    n = _load().or_sa_update(_gauge(gauge), vv, float(T), seed & (2**64 - 1), site, sweep, sub, copy, g)
+    return np.array(list(g)), n
 
 
 def anneal(U, gauge, T0, T1, n, sweep0=0, seed=0, copy=0):

@@ -564,22 +564,34 @@ static void micro_update(const double m[4], double g[4]) {
  * -(ln r1 + cos^2(2 pi r2) ln r3)/(2 alpha), accepted when
  * r4^2 <= 1 - delta.  READING: the heat-bath algorithm is not named in
  * Sec. 2.3; trials are capped at 64 and x0 = 1 is kept if none is accepted.
- * Returns the number of trials used (0 = cap hit). */
-int or_kp_sample(double alpha, uint64_t seed, uint32_t site, uint32_t sweep,
-                 uint32_t sub, uint32_t copy, double* x0) {
+ * Returns the number of trials used (0 = cap hit).  margin (may be NULL)
+ * receives the smallest |r4^2 - (1 - delta)| over the trials taken: how close
+ * the nearest accept/reject decision came to its threshold. */
+static int kp_sample(double alpha, uint64_t seed, uint32_t site, uint32_t sweep,
+                     uint32_t sub, uint32_t copy, double* x0, double* margin) {
+  double closest = INFINITY;
   for (int trial = 0; trial < KP_MAX_TRIALS; ++trial) {
     double ua[2], ub[2];
     draw2(seed, site, sweep, TAG_SA, sub, (uint32_t)(2 * trial), copy, ua);
     draw2(seed, site, sweep, TAG_SA, sub, (uint32_t)(2 * trial + 1), copy, ub);
     double c = cos(2.0 * M_PI * ua[1]);
     double delta = -(log(ua[0]) + c * c * log(ub[0])) / (2.0 * alpha);
+    double gap = fabs(ub[1] * ub[1] - (1.0 - delta));
+    if (gap < closest) closest = gap;
     if (ub[1] * ub[1] <= 1.0 - delta) {
       *x0 = 1.0 - 2.0 * delta;
+      if (margin) *margin = closest;
       return trial + 1;
     }
   }
   *x0 = 1.0;
+  if (margin) *margin = closest;
   return 0;
+}
+
+int or_kp_sample(double alpha, uint64_t seed, uint32_t site, uint32_t sweep,
+                 uint32_t sub, uint32_t copy, double* x0) {
+  return kp_sample(alpha, seed, site, sweep, sub, copy, x0, NULL);
 }
 
 /* Direction draw used by the Landau heat bath (draw index 128). */
@@ -589,16 +601,17 @@ int or_kp_sample(double alpha, uint64_t seed, uint32_t site, uint32_t sweep,
  * exp(Re tr(g W)/T) = exp(|m| (g.n)/T) with n = m/|m|.  Draw h with
  * h0 ~ sqrt(1-h0^2) exp(alpha h0), alpha = |m|/T, and a uniform direction,
  * then g = h n, so that g.n = h0. */
-static void sa_landau_update(const double m[4], double T, uint64_t seed,
-                             uint32_t site, uint32_t sweep, uint32_t sub,
-                             uint32_t copy, double g[4]) {
+static int sa_landau_update(const double m[4], double T, uint64_t seed,
+                            uint32_t site, uint32_t sweep, uint32_t sub,
+                            uint32_t copy, double g[4], double* margin) {
   double nm = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2] + m[3] * m[3]);
+  if (margin) *margin = INFINITY;
   if (nm == 0) {
     g[0] = 1; g[1] = g[2] = g[3] = 0;
-    return;
+    return 1;
   }
   double x0;
-  or_kp_sample(nm / T, seed, site, sweep, sub, copy, &x0);
+  int trials = kp_sample(nm / T, seed, site, sweep, sub, copy, &x0, margin);
   double u[2];
   draw2(seed, site, sweep, TAG_SA, sub, KP_DIRECTION_DRAW, copy, u);
   double cth = 2.0 * u[0] - 1.0;
@@ -614,6 +627,7 @@ static void sa_landau_update(const double m[4], double T, uint64_t seed,
   g[3] = cimag(G.m[0][0]);
   g[2] = creal(G.m[0][1]);
   g[1] = cimag(G.m[0][1]);
+  return trials;
 }
 
 /* cos(beta) with density proportional to exp(kappa cos(beta)) on [-1,1], by
@@ -658,10 +672,13 @@ static void sa_mag_update(const double x[3], double T, uint64_t seed,
 /* One subgroup step at one site: Step 1 (find g) and Step 2 (apply it to
  * the eight links U_mu(x) and U_mu(x - mu)) of Alg. 1.  For Coulomb the
  * local functional uses the spatial links only but g is applied to all four
- * directions, so the temporal links follow the gauge transformation. */
-void or_site_subgroup_update(const int dims[4], double* U, long s, int sub,
-                             int gauge, int algo, double param, uint32_t sweep,
-                             uint64_t seed, uint32_t copy) {
+ * directions, so the temporal links follow the gauge transformation.  For the
+ * Landau/Coulomb heat bath, trials/margin (may be NULL) receive the
+ * Kennedy-Pendleton trial count and decision margin of this update. */
+static void site_subgroup_update(const int dims[4], double* U, long s, int sub,
+                                 int gauge, int algo, double param,
+                                 uint32_t sweep, uint64_t seed, uint32_t copy,
+                                 int* trials, double* margin) {
   lattice L = make_lattice(dims);
   int i = SUBGROUP[sub][0], j = SUBGROUP[sub][1];
   double m[4], g[4], x[3] = {0, 0, 0};
@@ -694,12 +711,17 @@ void or_site_subgroup_update(const int dims[4], double* U, long s, int sub,
         or_update(m, 1.0, g);
       break;
     }
-    case OR_ALGO_SA:
+    case OR_ALGO_SA: {
+      int n = 1;
+      double gap = INFINITY;
       if (gauge == OR_MAG)
         sa_mag_update(x, param, seed, (uint32_t)s, sweep, (uint32_t)sub, copy, g);
       else
-        sa_landau_update(m, param, seed, (uint32_t)s, sweep, (uint32_t)sub, copy, g);
+        n = sa_landau_update(m, param, seed, (uint32_t)s, sweep, (uint32_t)sub, copy, g, &gap);
+      if (trials) *trials = n;
+      if (margin) *margin = gap;
       break;
+    }
     default:
       return;
   }
@@ -717,14 +739,25 @@ void or_site_subgroup_update(const int dims[4], double* U, long s, int sub,
   }
 }
 
+void or_site_subgroup_update(const int dims[4], double* U, long s, int sub,
+                             int gauge, int algo, double param, uint32_t sweep,
+                             uint64_t seed, uint32_t copy) {
+  site_subgroup_update(dims, U, s, sub, gauge, algo, param, sweep, seed, copy,
+                       NULL, NULL);
+}
+
 /* Checkerboard sweeps (Alg. 1): for each sweep, the even sublattice, then
  * the odd one; at each site the three subgroups in the order (0,1), (0,2),
  * (1,2) (READING: the order is not stated).  Random draws use the sweep
  * index sweep0 + k.  For Coulomb, slice_active (Nt flags, NULL = all) skips
- * time-slices that have stopped. */
-void or_sweep(const int dims[4], double* U, int gauge, int algo, double param,
-              int n_sweeps, uint32_t sweep0, uint64_t seed, uint32_t copy,
-              const int* slice_active) {
+ * time-slices that have stopped.  or_sweep_trace also records, for the last
+ * sweep and every (site, subgroup) in the order s*3 + sub, the heat-bath
+ * trial count (1 for MAG and for the other rules) and decision margin
+ * (infinite where no accept/reject decision was taken). */
+void or_sweep_trace(const int dims[4], double* U, int gauge, int algo,
+                    double param, int n_sweeps, uint32_t sweep0, uint64_t seed,
+                    uint32_t copy, const int* slice_active, int* trials,
+                    double* margin) {
   lattice L = make_lattice(dims);
   long V3 = L.V / L.n[0];
   for (int k = 0; k < n_sweeps; ++k)
@@ -736,10 +769,22 @@ void or_sweep(const int dims[4], double* U, int gauge, int algo, double param,
       for (long s = 0; s < L.V; ++s) {
         if (parity_of(&L, s) != p) continue;
         if (slice_active && !slice_active[s / V3]) continue;
-        for (int sub = 0; sub < 3; ++sub)
-          or_site_subgroup_update(dims, U, s, sub, gauge, algo, param,
-                                  sweep0 + (uint32_t)k, seed, copy);
+        for (int sub = 0; sub < 3; ++sub) {
+          int n = 1;
+          double gap = INFINITY;
+          site_subgroup_update(dims, U, s, sub, gauge, algo, param,
+                               sweep0 + (uint32_t)k, seed, copy, &n, &gap);
+          if (trials) trials[s * 3 + sub] = n;
+          if (margin) margin[s * 3 + sub] = gap;
+        }
       }
+}
+
+void or_sweep(const int dims[4], double* U, int gauge, int algo, double param,
+              int n_sweeps, uint32_t sweep0, uint64_t seed, uint32_t copy,
+              const int* slice_active) {
+  or_sweep_trace(dims, U, gauge, algo, param, n_sweeps, sweep0, seed, copy,
+                 slice_active, NULL, NULL);
 }
 
 /* Simulated annealing (Sec. 2.3): n heat-bath sweeps at temperatures
@@ -765,6 +810,21 @@ void or_step_quaternion(const double m[4], int algo, double param, double g[4]) 
     micro_update(m, g);
   else
     or_update(m, algo == OR_ALGO_OR ? param : 1.0, g);
+}
+
+/* The complete heat-bath update of one subgroup, exposed for the pins:
+ * Landau/Coulomb from the maximiser direction v = m (4 entries, unnormalised),
+ * MAG from the Pauli vector v = x (3 entries), at temperature T with the
+ * draws of (seed, site, sweep, sub, copy).  Returns the Kennedy-Pendleton
+ * trial count (Landau/Coulomb; 0 = cap hit) or 1 (MAG). */
+int or_sa_update(int gauge, const double v[4], double T, uint64_t seed,
+                 uint32_t site, uint32_t sweep, uint32_t sub, uint32_t copy,
+                 double g[4]) {
+  if (gauge == OR_MAG) {
+    sa_mag_update(v, T, seed, site, sweep, sub, copy, g);
+    return 1;
+  }
+  return sa_landau_update(v, T, seed, site, sweep, sub, copy, g, NULL);
 }
 
 /* The MAG maximiser for a Pauli vector x, exposed for the pins. */

@@ -177,6 +177,8 @@ struct gf_ctx {
   int prefetch = GF_PREFETCH_L2;  // how the sweep kernels fetch the next tile
   int stage_wait_polls = -1;      // polls of a staging wait (< 0: the kernel's default)
   int fused_obs = 1;       // F/theta fused into the last OR sweep where possible
+  int sa_micro = 3;        // microcanonical sweeps after each heat-bath sweep (Sec. 2.3)
+  int* sa_trace_d = nullptr;  // caller's device buffer for heat-bath trial counts, or nullptr
   int lpt[2][5] = {{0}};  // [fp64][algo] chosen links per thread, 0 = default
   int pmode[2][5] = {{0}};  // [fp64][algo] tile fetch chosen by gf_autotune + 1, 0 = the context's
   // optional per-kernel timing: CUDA events around every launch of a class
@@ -279,6 +281,7 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     a.obs_site = static_cast<double2*>(c->obs_site);
     a.err = c->err_d;
     a.wait_polls = -1;
+    a.sa_trace = kalgo == gfk::ALG_SA ? c->sa_trace_d : nullptr;
     cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<double>(a, c->gauge, kalgo, lpt, c->st);
     prof_end(c, t0, GF_KERNEL_SWEEP_FP64);
@@ -303,6 +306,7 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     a.obs_site = static_cast<double2*>(c->obs_site);
     a.err = c->err_d;
     a.wait_polls = c->stage_wait_polls;
+    a.sa_trace = kalgo == gfk::ALG_SA ? c->sa_trace_d : nullptr;
     if (a.prefetch == GF_PREFETCH_SMEM) c->err_pending = true;
     cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<float>(a, c->gauge, kalgo, lpt, c->st);
@@ -676,7 +680,7 @@ int check_algo_param(int algo, double param) {
   return fail(GF_EINVAL, "bad algorithm %d", algo);
 }
 
-// One API-level sweep: SA = heat bath + 3 microcanonical sweeps.
+// One API-level sweep: SA = heat bath + sa_micro (3) microcanonical sweeps.
 int api_sweep(gf_ctx* c, int algo, double param, uint64_t seed, bool obs_last = false) {
   switch (algo) {
     case GF_RELAX: return full_sweep(c, gfk::ALG_OR, GF_RELAX, 1.0, seed, 0, obs_last);
@@ -685,7 +689,7 @@ int api_sweep(gf_ctx* c, int algo, double param, uint64_t seed, bool obs_last = 
     case GF_SR: return full_sweep(c, gfk::ALG_SR, GF_SR, param, seed);
     case GF_SA: {
       int r = full_sweep(c, gfk::ALG_SA, GF_SA, param, seed);
-      for (int k = 0; k < 3 && !r; ++k) r = full_sweep(c, gfk::ALG_MICRO, GF_MICRO, 0.0, seed);
+      for (int k = 0; k < c->sa_micro && !r; ++k) r = full_sweep(c, gfk::ALG_MICRO, GF_MICRO, 0.0, seed);
       return r;
     }
   }
@@ -1033,6 +1037,22 @@ int gf_set_copy_base(gf_ctx* c, uint32_t base) {
   return GF_OK;
 }
 
+int gf_set_sa_micro(gf_ctx* c, int n_micro) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (n_micro < 0 || n_micro > 64) return fail(GF_EINVAL, "n_micro = %d not in [0, 64]", n_micro);
+  c->sa_micro = n_micro;
+  return GF_OK;
+}
+
+int gf_set_sa_trace(gf_ctx* c, int* device_counts) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (((uintptr_t)device_counts & 3) != 0) return fail(GF_EINVAL, "device_counts must be 4-byte aligned");
+  c->sa_trace_d = device_counts;
+  return GF_OK;
+}
+
 int gf_set_fused_observables(gf_ctx* c, int on) {
   int r = check_ctx(c);
   if (r) return r;
@@ -1334,14 +1354,16 @@ int gf_protocol(gf_ctx* c, const gf_protocol_params* P, gf_fix_result* res) {
       const double T = P->sa_steps > 1 ? P->T_start + (P->T_end - P->T_start) * k / (double)(P->sa_steps - 1)
                                        : P->T_start;
       if ((r = api_sweep(c, GF_SA, T, P->seed))) return r;
-      R.sweeps += 4;
-      R.site_updates += 4 * sites;
+      const int per_step = 1 + c->sa_micro;
+      R.sweeps += per_step;
+      R.site_updates += (uint64_t)per_step * sites;
       if (c->prec != GF_FP64 && !c->fp64) {
-        R.sweeps_fp32 += 4;
-        if (P->fix.reunit_interval > 0 && (k + 1) * 4 % P->fix.reunit_interval < 4 && (r = reunitarize(c)))
+        R.sweeps_fp32 += per_step;
+        if (P->fix.reunit_interval > 0 && (k + 1) * per_step % P->fix.reunit_interval < per_step &&
+            (r = reunitarize(c)))
           return r;
       } else {
-        R.sweeps_fp64 += 4;
+        R.sweeps_fp64 += per_step;
       }
     }
   }

@@ -303,9 +303,10 @@ __device__ __forceinline__ quat<R> mag_micro(R x1, R x2, R x3, R r) {
 }
 
 // Kennedy-Pendleton heat bath for x0 ~ sqrt(1-x0^2) exp(alpha x0), at most
-// KP_TRIALS trials (x0 = 1 if none is accepted).
+// KP_TRIALS trials (x0 = 1 if none is accepted); trials receives the number
+// of trials used (0 if none was accepted).
 template <typename R>
-__device__ __forceinline__ R kp_sample(R alpha, const Rng& rng, uint32_t sub) {
+__device__ __forceinline__ R kp_sample(R alpha, const Rng& rng, uint32_t sub, int& trials) {
   for (int t = 0; t < KP_TRIALS; ++t) {
     double a1, a2, b1, b2;
     rng.draw2(TAG_SA, sub, (uint32_t)(2 * t), a1, a2);
@@ -314,19 +315,24 @@ __device__ __forceinline__ R kp_sample(R alpha, const Rng& rng, uint32_t sub) {
     sincos2pi((R)a2, s, c);
     R delta = -(log_((R)a1) + c * c * log_((R)b1)) / (R(2) * alpha);
     R r4 = (R)b2;
-    if (r4 * r4 <= R(1) - delta) return R(1) - R(2) * delta;
+    if (r4 * r4 <= R(1) - delta) {
+      trials = t + 1;
+      return R(1) - R(2) * delta;
+    }
   }
+  trials = 0;
   return R(1);
 }
 
 // Landau/Coulomb heat bath: g = h m/|m| with h0 from Kennedy-Pendleton at
 // alpha = |m|/T and a uniform direction for the vector part.
 template <typename R>
-__device__ __forceinline__ quat<R> rule_sa_landau(quat<R> m, R T, const Rng& rng, uint32_t sub) {
+__device__ __forceinline__ quat<R> rule_sa_landau(quat<R> m, R T, const Rng& rng, uint32_t sub, int& trials) {
   R n2 = m.q0 * m.q0 + m.q1 * m.q1 + m.q2 * m.q2 + m.q3 * m.q3;
+  trials = 1;
   if (n2 == R(0)) return qidentity<R>();
   R nm = sqrt_(n2);
-  R x0 = kp_sample<R>(nm / T, rng, sub);
+  R x0 = kp_sample<R>(nm / T, rng, sub, trials);
   double ua, ub;
   rng.draw2(TAG_SA, sub, KP_DIR_DRAW, ua, ub);
   R cth = R(2) * (R)ua - R(1);

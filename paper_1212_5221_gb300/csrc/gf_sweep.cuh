@@ -30,6 +30,8 @@ struct SweepArgs {
   int* err;           // set to 1 if a shared-memory staging wait ran out (prefetch 2)
   int wait_polls;     // polls of a staging wait before it gives up: < 0 the default
                       // (2^24, about 2 s), 0 none (the wait runs out at once)
+  int* sa_trace;      // heat bath only, or nullptr: [copy][site][subgroup] Kennedy-Pendleton
+                      // trial counts (0 = none accepted; MAG: 1), written by lane 0
 };
 
 // Per-site FP64 observables of the MAG form from the slot matrices M
@@ -453,6 +455,7 @@ __device__ __forceinline__ void sweep_site_mag(const SweepArgs<R>& a, uint32_t c
       g = ((R)ua < a.param) ? mag_micro(x1, x2, x3, r) : rule_or(m, R(1));
     } else {
       g = rule_sa_mag(m, r, a.param, rng, (uint32_t)sub);
+      if (a.sa_trace && valid && lane == 0) a.sa_trace[((size_t)copy * G.V + s) * 3 + sub] = 1;
     }
 #pragma unroll
     for (int j = 0; j < LPT; ++j) left_subgroup_mult(u[j], i, j2, g);
@@ -498,7 +501,7 @@ __device__ __forceinline__ su2m<R> su2_of(const quat<R>& g) {
 // Re tr(g W) and the update rule of the algorithm.
 template <typename R, int ALGO>
 __device__ __forceinline__ quat<R> choose_k(cx<R> W00, cx<R> W01, cx<R> W10, cx<R> W11, R param, const Rng& rng,
-                                            uint32_t sub) {
+                                            uint32_t sub, int* trace) {
   const quat<R> m{W00.re + W11.re, -(W01.im + W10.im), -(W01.re - W10.re), -(W00.im - W11.im)};
   if (ALGO == ALG_OR) return rule_or(m, param);
   if (ALGO == ALG_MICRO) return rule_micro(m);
@@ -507,7 +510,10 @@ __device__ __forceinline__ quat<R> choose_k(cx<R> W00, cx<R> W01, cx<R> W10, cx<
     rng.draw2(TAG_SR, sub, 0, ua, ub);
     return ((R)ua < param) ? rule_micro(m) : rule_or(m, R(1));
   }
-  return rule_sa_landau(m, param, rng, sub);
+  int trials;
+  const quat<R> g = rule_sa_landau(m, param, rng, sub, trials);
+  if (trace) trace[sub] = trials;
+  return g;
 }
 
 // FP64 contribution of a slot to K, from its stored rows (row 2 rebuilt in
@@ -702,7 +708,9 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
 
   // Step 1: the three subgroups in the order (0,1), (0,2), (1,2)
   Rng rng{a.k0, a.k1, s, a.sweep, a.copy0 + copy};
-  const su2m<R> h0 = su2_of(choose_k<R, ALGO>(K.e[0][0], K.e[0][1], K.e[1][0], K.e[1][1], a.param, rng, 0u));
+  int* trace = (ALGO == ALG_SA && a.sa_trace && valid && lane == 0) ? a.sa_trace + ((size_t)copy * Gm.V + s) * 3
+                                                                     : nullptr;
+  const su2m<R> h0 = su2_of(choose_k<R, ALGO>(K.e[0][0], K.e[0][1], K.e[1][0], K.e[1][1], a.param, rng, 0u, trace));
   {  // K <- g0 K on the entries read later: row 0, and row 1 columns 1, 2
     cx<R> r0[3];
 #pragma unroll
@@ -712,10 +720,10 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
 #pragma unroll
     for (int y = 0; y < 3; ++y) K.e[0][y] = r0[y];
   }
-  const su2m<R> h1 = su2_of(choose_k<R, ALGO>(K.e[0][0], K.e[0][2], K.e[2][0], K.e[2][2], a.param, rng, 1u));
+  const su2m<R> h1 = su2_of(choose_k<R, ALGO>(K.e[0][0], K.e[0][2], K.e[2][0], K.e[2][2], a.param, rng, 1u, trace));
 #pragma unroll
   for (int y = 1; y < 3; ++y) K.e[2][y] = cmul2(h1.h10, K.e[0][y], h1.h11, K.e[2][y]);  // row 2 of g1 K
-  const su2m<R> h2 = su2_of(choose_k<R, ALGO>(K.e[1][1], K.e[1][2], K.e[2][1], K.e[2][2], a.param, rng, 2u));
+  const su2m<R> h2 = su2_of(choose_k<R, ALGO>(K.e[1][1], K.e[1][2], K.e[2][1], K.e[2][2], a.param, rng, 2u, trace));
 
   // G = g2 g1 g0 in the 3x3 embedding
   mat3<R> G;

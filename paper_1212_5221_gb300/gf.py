@@ -113,6 +113,8 @@ _SIG = {
     "gf_random_gauge_transform_async": [_P, ctypes.c_uint64],
     "gf_synchronize": [_P],
     "gf_set_fused_observables": [_P, _I],
+    "gf_set_sa_micro": [_P, _I],
+    "gf_set_sa_trace": [_P, _P],
     "gf_get_links_per_thread": [_P, _PI],
     "gf_autotune": [_P, _I, _PI, _PD],
     "gf_fix": [_P, ctypes.POINTER(gf_fix_params), ctypes.POINTER(gf_fix_result)],
@@ -372,6 +374,17 @@ def gf_set_prefetch(h, mode=GF_PREFETCH_L2):
 
 def gf_set_fused_observables(h, on=True):
     _check(lib().gf_set_fused_observables(h, 1 if on else 0), "gf_set_fused_observables")
+
+
+def gf_set_sa_micro(h, n_micro=3):
+    """Microcanonical sweeps after each heat-bath sweep (3 by default; 0 = heat bath alone)."""
+    _check(lib().gf_set_sa_micro(h, int(n_micro)), "gf_set_sa_micro")
+
+
+def gf_set_sa_trace(h, device_ptr):
+    """Record heat-bath trial counts into int32 device memory of n_copies*V*3
+    entries ([copy][site][subgroup]); 0 or None turns the record off."""
+    _check(lib().gf_set_sa_trace(h, ctypes.c_void_p(int(device_ptr) if device_ptr else 0)), "gf_set_sa_trace")
 
 
 def gf_get_links_per_thread(h):

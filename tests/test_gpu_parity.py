@@ -183,6 +183,101 @@ def test_single_sa_sweep(gf, synth, orc, gauge, prec, lpt):
         assert np.median(d) <= max(2e-5, 3 * np.median(env))
 
 
+def _near(mask_sites, dims, radius=2):
+    """Sites within lattice distance `radius` (periodic) of any site in the mask."""
+    m = mask_sites.reshape(dims)
+    out = m.copy()
+    for _ in range(radius):
+        grown = out.copy()
+        for ax in range(4):
+            grown |= np.roll(out, 1, ax) | np.roll(out, -1, ax)
+        out = grown
+    return out.reshape(-1)
+
+
+def _heat_bath_pair(gf, orc, U, dims, gauge, prec, T, seed, lpt=0):
+    """One heat-bath sweep alone on both sides; returns the oracle's links,
+    trial counts and margins, the kernel's links and trial counts."""
+    import torch
+
+    V = int(np.prod(dims))
+    W = U.copy()
+    t_o, m_o = orc.sweep_trace(W, gauge, "sa", T, 1, 0, seed)
+    buf = torch.full((V * 3,), -7, dtype=torch.int32, device="cuda")
+    with Ctx(gf, dims, gauge, prec) as h:
+        if lpt:
+            gf.gf_set_links_per_thread(h, lpt)
+        gf.gf_set_sa_micro(h, 0)
+        gf.gf_set_sa_trace(h, buf.data_ptr())
+        gf.gf_load_links(h, 0, U)
+        gf.gf_sweep(h, "sa", T, 1, seed, observables=False)
+        assert gf.gf_get_sweep_index(h) == 1
+        gf.gf_set_sa_trace(h, None)
+        Vg = store(gf, h, dims)
+    t_g = buf.cpu().numpy().reshape(V, 3)
+    return W, t_o, m_o, Vg, t_g
+
+
+# The heat bath's accept/reject decisions may differ between the kernel and
+# the oracle only where the oracle's decision lay this close to its threshold:
+# FP64 decides in FP64 on inputs equal to rounding (transcendentals differ by
+# an ulp or two); FP32 decides in FP32 on FP32-rounded links, whose alpha and
+# uniforms carry relative errors of a few 1e-7.
+DECISION_MARGIN = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+@pytest.mark.parametrize("lpt", [1, 8])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("T", [0.3, 2.0])
+@pytest.mark.parametrize("gauge", GAUGES)
+def test_heat_bath_sweep(gf, synth, orc, gauge, T, prec, lpt):
+    """One heat-bath sweep without the microcanonical sweeps (Sec. 2.3), the
+    same Philox draws on both sides.  Every Kennedy-Pendleton decision (trial
+    count per site and subgroup) is the oracle's, except where the oracle's
+    decision lay within DECISION_MARGIN of its threshold; links agree to
+    1e-12 (FP64) / the FP32 single-sweep bound away from any such site."""
+    U = rough(synth, orc, DIMS, 0.5, 4, 12)
+    W, t_o, m_o, Vg, t_g = _heat_bath_pair(gf, orc, U, DIMS, gauge, prec, T, 7, lpt)
+    assert (t_g >= 0).all() and (t_g <= 64).all()
+    flips = t_g != t_o
+    assert (m_o[flips] < DECISION_MARGIN[prec]).all(), (t_g[flips], t_o[flips], m_o[flips])
+    if prec == "fp64":
+        assert flips.sum() == 0
+    far = ~_near(flips.any(1), DIMS)
+    tol = TOL[prec]
+    if prec == "fp32":
+        # the oracle's own response to FP32-rounded input, away from any
+        # decision that rounding alone flips
+        R = round_to_fp32(U)
+        t_r, _ = orc.sweep_trace(R, gauge, "sa", T, 1, 0, 7)
+        far &= ~_near((t_r != t_o).any(1), DIMS)
+        tol = max(tol, 2.5 * np.abs(R - W).reshape(-1, 36).max(1)[far].max())
+    assert far.mean() > 0.5
+    d = np.abs(Vg - W).reshape(-1, 36).max(1)[far]
+    assert d.max() <= tol, (d.max(), tol)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_heat_bath_decisions_large_sample(gf, synth, orc, prec):
+    """The accept/reject decisions of the Landau/Coulomb heat bath over about
+    1.2 million site-subgroup updates (16^4, two gauges, three temperatures):
+    at most 1e-6 of them (FP64; FP32: 1e-4) may differ from the oracle's, and
+    each one that does lies within DECISION_MARGIN of its threshold."""
+    dims = (16, 16, 16, 16)
+    U = rough(synth, orc, dims, 0.4, 6, 14)
+    n = flips_total = 0
+    for gauge in ("landau", "coulomb"):
+        for T, seed in ((0.3, 31), (1.0, 32), (3.0, 33)):
+            W, t_o, m_o, Vg, t_g = _heat_bath_pair(gf, orc, U, dims, gauge, prec, T, seed)
+            flips = t_g != t_o
+            assert (m_o[flips] < DECISION_MARGIN[prec]).all(), (gauge, T, m_o[flips])
+            n += t_o.size
+            flips_total += int(flips.sum())
+            if prec == "fp64" and not flips.any():
+                assert np.abs(Vg - W).max() <= TOL["fp64"]
+    assert flips_total <= (1e-6 if prec == "fp64" else 1e-4) * n, (flips_total, n)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("gauge", GAUGES)
 def test_ten_sweeps_and_observables(gf, synth, orc, gauge, prec):

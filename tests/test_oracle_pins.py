@@ -572,3 +572,111 @@ def test_annealing_cold_limit_and_hot_moves(orc, synth, gauge):
     orc.sweep(C, gauge, "sa", 2.0 if gauge == "landau" else 1e4, 2, 0, 9)
     assert orc.observables(C, gauge)[0] < orc.observables(B, gauge)[0] - 0.1
     assert orc.unitarity(C)[1] < 1e-13
+
+
+# --------------------------------------------------------------------------
+# The complete heat-bath updates (Sec. 2.3): the distribution of g itself
+
+
+def _qmul(a, b):
+    """Quaternion product matching the Cayley-Klein matrix product."""
+    return np.array([a[0] * b[0] - a[1:] @ b[1:],
+                     *(a[0] * b[1:] + b[0] * a[1:] - np.cross(a[1:], b[1:]))])
+
+
+def _qconj(a):
+    return np.array([a[0], -a[1], -a[2], -a[3]])
+
+
+def _landau_moments(alpha):
+    """E[x] and E[x^2] under the density sqrt(1-x^2) exp(alpha x) on [-1, 1]:
+    the law of g.n when g is Haar on SU(2) = S^3 weighted by exp(alpha g.n)."""
+    w = lambda x, k: x**k * np.sqrt(1 - x * x) * np.exp(alpha * (x - 1))
+    Z = integrate.quad(w, -1, 1, args=(0,), limit=200)[0]
+    return (integrate.quad(w, -1, 1, args=(1,), limit=200)[0] / Z,
+            integrate.quad(w, -1, 1, args=(2,), limit=200)[0] / Z)
+
+
+@pytest.mark.parametrize("alpha", [0.8, 4.0])
+def test_landau_heat_bath_update_distribution(orc, alpha):
+    """g from the full Landau heat-bath update must be distributed as
+    exp(Re tr(gW)/T) times the Haar measure, i.e. exp(alpha g.n) on S^3 with
+    n = m/|m| and alpha = |m|/T.  Checked independently of the sampler's
+    parts: the law of g.n (chi^2 against the density), the direction of the
+    remainder h = g n^-1 (uniform on S^2: KS of its z component against
+    U(-1,1) and of its azimuth), and the first two moments of g, E[g] = E[x] n
+    and E[g g^T] = E[x^2] n n^T + (1 - E[x^2])/3 (1 - n n^T), with E[x], E[x^2]
+    from quadrature.  A direction draw on half the sphere, a wrong sign of the
+    weight, or composing with the conjugate maximiser fails one of these."""
+    n_samples = 40000
+    m = np.array([0.7, -1.1, 0.4, 1.9])
+    nvec = m / np.linalg.norm(m)
+    T = np.linalg.norm(m) / alpha
+    G = np.array([orc.sa_update("landau", m, T, 11, s, 3, 1)[0] for s in range(n_samples)])
+    assert np.abs(np.linalg.norm(G, axis=1) - 1).max() < 1e-14
+    x = G @ nvec
+    Ex, Ex2 = _landau_moments(alpha)
+    pdf = lambda t: np.sqrt(1 - t * t) * np.exp(alpha * (t - 1))
+    Z = integrate.quad(pdf, -1, 1, limit=200)[0]
+    edges = np.quantile(x, np.linspace(0, 1, 31))
+    edges[0], edges[-1] = -1, 1
+    obs = np.histogram(x, edges)[0]
+    exp = np.array([integrate.quad(pdf, a, b)[0] / Z for a, b in zip(edges[:-1], edges[1:])]) * n_samples
+    chi2 = ((obs - exp) ** 2 / exp).sum()
+    assert stats.chi2.sf(chi2, len(obs) - 1) > 1e-4
+    H = np.array([_qmul(g, _qconj(nvec)) for g in G])
+    assert np.abs(H[:, 0] - x).max() < 1e-14  # g = h n with h0 = g.n
+    d = H[:, 1:] / np.linalg.norm(H[:, 1:], axis=1, keepdims=True)
+    assert stats.kstest(d[:, 2], stats.uniform(-1, 2).cdf).pvalue > 1e-4
+    assert stats.kstest(np.arctan2(d[:, 1], d[:, 0]), stats.uniform(-np.pi, 2 * np.pi).cdf).pvalue > 1e-4
+    se = 1 / np.sqrt(n_samples)
+    assert np.abs(G.mean(0) - Ex * nvec).max() < 5 * se
+    M2 = G.T @ G / n_samples
+    P = np.outer(nvec, nvec)
+    assert np.abs(M2 - (Ex2 * P + (1 - Ex2) / 3 * (np.eye(4) - P))).max() < 5 * se
+
+
+def _adjoint(g, x):
+    """Pauli vector of G (x.sigma) G^dag for the Cayley-Klein matrix G of g."""
+    sig = [np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.array([[1, 0], [0, -1]])]
+    Gm = cayley_klein(g)
+    X = sum(xi * s for xi, s in zip(x, sig))
+    Y = Gm @ X @ Gm.conj().T
+    return np.array([Y[0, 1].real, -Y[0, 1].imag, 0.5 * (Y[0, 0] - Y[1, 1]).real])
+
+
+@pytest.mark.parametrize("kappa", [0.3, 5.0])
+def test_mag_heat_bath_update_distribution(orc, kappa):
+    """The MAG heat bath weights g by exp((R(g) x)_3 / T) times the Haar
+    measure (the local functional is const + (R(g) x)_3).  Under Haar g the
+    rotated direction R(g) x/|x| is uniform on S^2, so its polar cosine must
+    follow exp(kappa cos(beta)), kappa = |x|/T, and its azimuth must be
+    uniform.  Both are checked on y = R(g) x computed from the matrices, which
+    pins the composition g = r h1 as a whole (the other order, or a rotation
+    that does not start from the maximiser, fails)."""
+    n_samples = 20000
+    x = np.array([0.4, -0.9, -1.3])
+    T = np.linalg.norm(x) / kappa
+    Y = np.array([_adjoint(orc.sa_update("mag", x, T, 5, s, 2, 0)[0], x) for s in range(n_samples)])
+    assert np.abs(np.linalg.norm(Y, axis=1) - np.linalg.norm(x)).max() < 1e-13
+    cb = Y[:, 2] / np.linalg.norm(x)
+    cdf = lambda c: np.expm1(kappa * (c + 1)) / np.expm1(2 * kappa)
+    assert stats.kstest(cb, cdf).pvalue > 1e-4
+    phi = np.arctan2(Y[:, 1], Y[:, 0])
+    assert stats.kstest(phi, stats.uniform(-np.pi, 2 * np.pi).cdf).pvalue > 1e-4
+
+
+def test_heat_bath_sweep_trace(orc, synth):
+    """The traced sweep reports one Kennedy-Pendleton decision record per
+    (site, subgroup): trial counts in 1..64 (0 only at the cap), a margin
+    that is non-negative, and the same links as the plain sweep."""
+    U = rough_field(synth, orc, (4, 4, 4, 4), 0.4, 1, 2)
+    A, B = U.copy(), U.copy()
+    trials, margin = orc.sweep_trace(A, "landau", "sa", 0.7, 1, 0, 21)
+    orc.sweep(B, "landau", "sa", 0.7, 1, 0, 21)
+    assert np.array_equal(A, B)
+    assert trials.shape == (256, 3) and trials.min() >= 0 and trials.max() <= 64
+    assert (margin >= 0).all() and np.isfinite(margin).all()
+    assert trials.mean() > 1.0  # at T = 0.7 some proposals are rejected
+    t2, m2 = orc.sweep_trace(U.copy(), "mag", "sa", 0.7, 1, 0, 21)
+    assert (t2 == 1).all() and np.isinf(m2).all()
