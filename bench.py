@@ -546,15 +546,17 @@ def run_precision_study(args):
     iterations of a 32^4 Landau problem (the shapes of Sec. 4.5's two
     figures, on a synthetic field): FP64 with and without re-unitarisation
     every 100 iterations, FP32 (rows re-projected at every load) with and
-    without FP64 re-unitarisation every 100, and GF_MIXED (FP64 master moved
-    by exact transformations, synced every 100)."""
+    without FP64 re-unitarisation every 100, the paper's MP (Step 1 in FP64
+    on FP32 links, Step 2 in FP32) with and without it, and GF_MIXED (FP64
+    master moved by exact transformations, synced every 100)."""
     from paper_1212_5221_gb300 import build, gf, inputs
 
     build.build_all()
     dims, n_iter, every = (32, 32, 32, 32), args.study_iters, args.study_every
     U = inputs.links(dims, "smooth", 0.3, 1)
     variants = [("fp64_reunit100", "fp64", True), ("fp64", "fp64", False), ("fp32_reunit100", "fp32", True),
-                ("fp32", "fp32", False), ("mixed", "mixed", True)]
+                ("fp32", "fp32", False), ("mp_reunit100", "mp", True), ("mp", "mp", False),
+                ("mixed", "mixed", True)]
     V = np.empty(tuple(dims) + (4, 3, 3), np.complex128)
     rows = {}
     for name, prec, reunit in variants:

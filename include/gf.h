@@ -54,8 +54,13 @@ typedef enum { GF_LANDAU = 0, GF_COULOMB = 1, GF_MAG = 2 } gf_gauge;
  * whenever the links are read, and the FP32 copy is re-rounded from it, so
  * the master never leaves the gauge orbit of the input.  The final sweeps
  * run on the FP64 master (gf_promote / gf_fix).  Reductions are always FP64.
- * GF_MIXED is not the paper's "MP" (Sec. 4.5: Step 1 in DP, Step 2 in SP). */
-typedef enum { GF_FP64 = 0, GF_FP32 = 1, GF_MIXED = 2 } gf_precision;
+ * GF_MP is the paper's mixed precision "MP" (Sec. 4.5): links stored in FP32
+ * (12 reals), the local update (Step 1 of Alg. 1: the gathered K or MAG
+ * vector, the subgroup choices and their product) computed in FP64 from
+ * them, and its application to the links (Step 2) in FP32; it has no FP64
+ * copy and no switch.  Its convergence checks read the links in a separate
+ * FP64 pass (no fused variant). */
+typedef enum { GF_FP64 = 0, GF_FP32 = 1, GF_MIXED = 2, GF_MP = 3 } gf_precision;
 
 /* Local update (Step 1 of Alg. 1): relaxation (Eq. localsolution per SU(2)
  * subgroup), overrelaxation g -> g^omega to first order (Sec. 2.2.3, in
@@ -164,6 +169,57 @@ int gf_set_sa_micro(gf_ctx* ctx, int n_micro);
  *                  off.  Entries of sites not updated are left as they were.
  * GF_EINVAL if the pointer is not 4-byte aligned. */
 int gf_set_sa_trace(gf_ctx* ctx, int* device_counts);
+
+/* ---- Time-slab decomposition of one Landau or MAG lattice (Sec. 5) -------
+ * The lattice is split along t into slabs of nt consecutive time-slices, one
+ * per process (one GPU each).  A site's update reads U_0(x - 0) from the
+ * slice below it, so a process also keeps a copy of the slice below its slab
+ * and, after every half-sweep, exchanges with its two ring neighbours the
+ * temporal links on the slab boundaries that the half-sweep changed
+ * (Sec. 5.1): each message is U_0, rows 0 and 1, of the sites of one parity
+ * of one slice, 1/12 of a time-slice (Sec. 5.2).  Communication is the
+ * caller's (the Python module paper_1212_5221_gb300.slab runs the schedule
+ * over torch.distributed); these calls do the device part.
+ *
+ * gf_set_slab turns a context of local dims (nt + 2, Nx, Ny, Nz), n_copies 1,
+ * GF_LANDAU or GF_MAG, GF_FP64 or GF_FP32 storage, into the slab owning the
+ * global time-slices [t0, t0 + nt) of a lattice with Nt_global slices (even,
+ * >= nt): local slice 0 holds global slice t0 - 1 (mod Nt_global), local
+ * slices 1 .. nt the owned ones, local slice nt + 1 is never read.  Load the
+ * context with those nt + 2 global slices (natural order) by gf_load_links.
+ * Random draws then use global site indices, so every slab draws what the
+ * whole lattice would.  Whole-lattice sweeps (gf_sweep, gf_fix, gf_anneal,
+ * gf_protocol and their _async forms) and gf_random_gauge_transform return
+ * GF_EINVAL on a slab.  GF_EINVAL for any other shape, gauge or storage. */
+int gf_set_slab(gf_ctx* ctx, int t0, int Nt_global);
+
+/* Which owned slices gf_sweep_half updates. */
+enum { GF_SLAB_OWNED = 0, GF_SLAB_BOUNDARY = 1, GF_SLAB_INNER = 2 };
+
+/* One half-sweep (Alg. 1 for the sites of one parity): the sites of GLOBAL
+ * parity `parity` of the owned slices (part GF_SLAB_OWNED), of the first and
+ * last owned slice only (GF_SLAB_BOUNDARY), or of the others
+ * (GF_SLAB_INNER), so that the boundary can be updated and sent while the
+ * inner slices run (Sec. 5.3).  On a context that is not a slab, part must
+ * be GF_SLAB_OWNED and the whole lattice is swept.  algo/param as gf_sweep,
+ * except that GF_SA is the heat bath alone.  Draws use the context's sweep
+ * index, which this call leaves unchanged (advance it with
+ * gf_set_sweep_index once both halves are done).  Enqueued on the context's
+ * stream; returns without waiting. */
+int gf_sweep_half(gf_ctx* ctx, gf_algo algo, double param, int parity, int part, uint64_t seed);
+
+/* Bytes of one boundary message: 3 (FP32) or 6 (FP64) x Nx*Ny*Nz/2 x 16. */
+int gf_slab_bytes(gf_ctx* ctx, size_t* bytes);
+
+/* Copy U_0 (rows 0 and 1, as stored) of the sites of global parity `parity`
+ * in local time-slice `slice` into buf (gf_slab_pack) or from buf into the
+ * links (gf_slab_unpack).  buf: gf_slab_bytes bytes of device or host memory
+ * owned by the caller, layout [chunk][site of that parity in the slice].
+ * Enqueued on the context's stream (synchronise before reading buf on the
+ * host).  GF_EINVAL for a slice outside [0, local Nt) or a GF_MIXED context
+ * in its FP32 stage. */
+int gf_slab_pack(gf_ctx* ctx, int slice, int parity, void* buf);
+int gf_slab_unpack(gf_ctx* ctx, int slice, int parity, const void* buf);
 
 /* Re-unitarise every stored matrix in FP64: normalise row 0, Gram-Schmidt
  * row 1, normalise; row 2 = conj(row0 x row1) (Sec. 4.5, reprojection). */

@@ -86,6 +86,8 @@ def _load():
                             _U32, _V]),
         "or_sweep_trace": (None, [_PI, _V, ctypes.c_int, ctypes.c_int, _D, ctypes.c_int, _U32, _U64,
                                   _U32, _V, _V, _V]),
+        "or_half_sweep": (None, [_PI, _V, ctypes.c_int, ctypes.c_int, _D, ctypes.c_int, _U32, _U64,
+                                 _U32, _V]),
         "or_sa_update": (ctypes.c_int, [ctypes.c_int, _PD, _D, _U64, _U32, _U32, _U32, _U32, _PD]),
         "or_anneal": (None, [_PI, _V, ctypes.c_int, _D, _D, ctypes.c_int, _U32, _U64, _U32]),
         "or_step_quaternion": (None, [_PD, ctypes.c_int, _D, _PD]),
@@ -235,6 +237,17 @@ def sweep_trace(U, gauge, algo, param=1.0, n=1, sweep0=0, seed=0, copy=0, slice_
                            seed & (2**64 - 1), copy, None if act is None else act.ctypes.data,
                            trials.ctypes.data, margin.ctypes.data)
     return trials, margin
+
+
+def half_sweep(U, gauge, algo, param, parity, sweep=0, seed=0, copy=0, slice_active=None):
+    """The sites of one parity only (half of a checkerboard sweep), draws of `sweep`."""
+    act = None
+    if slice_active is not None:
+        act = np.ascontiguousarray(slice_active, dtype=np.int32)
+        if act.shape != (U.shape[0],):
+            raise ValueError("slice_active needs one flag per time-slice")
+    _load().or_half_sweep(_dims(U), U.ctypes.data, _gauge(gauge), _algo(algo), param, parity, sweep,
+                          seed & (2**64 - 1), copy, None if act is None else act.ctypes.data)
 
 
 def sa_update(gauge, v, T, seed, site, sweep=0, sub=0, copy=0):

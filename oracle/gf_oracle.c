@@ -754,30 +754,50 @@ void or_site_subgroup_update(const int dims[4], double* U, long s, int sub,
  * sweep and every (site, subgroup) in the order s*3 + sub, the heat-bath
  * trial count (1 for MAG and for the other rules) and decision margin
  * (infinite where no accept/reject decision was taken). */
+/* One half of a sweep: the sites of parity p (Alg. 1's inner loop). */
+static void half_sweep(const lattice* L, const int dims[4], double* U, int gauge,
+                       int algo, double param, int p, uint32_t sweep,
+                       uint64_t seed, uint32_t copy, const int* slice_active,
+                       int* trials, double* margin) {
+  long V3 = L->V / L->n[0];
+  /* sites of one parity touch disjoint links (Sec. 2.2): a build with
+   * -fopenmp may visit them in parallel with the same result; the plain
+   * build ignores the pragma */
+#pragma omp parallel for schedule(static)
+  for (long s = 0; s < L->V; ++s) {
+    if (parity_of(L, s) != p) continue;
+    if (slice_active && !slice_active[s / V3]) continue;
+    for (int sub = 0; sub < 3; ++sub) {
+      int n = 1;
+      double gap = INFINITY;
+      site_subgroup_update(dims, U, s, sub, gauge, algo, param, sweep, seed,
+                           copy, &n, &gap);
+      if (trials) trials[s * 3 + sub] = n;
+      if (margin) margin[s * 3 + sub] = gap;
+    }
+  }
+}
+
 void or_sweep_trace(const int dims[4], double* U, int gauge, int algo,
                     double param, int n_sweeps, uint32_t sweep0, uint64_t seed,
                     uint32_t copy, const int* slice_active, int* trials,
                     double* margin) {
   lattice L = make_lattice(dims);
-  long V3 = L.V / L.n[0];
   for (int k = 0; k < n_sweeps; ++k)
     for (int p = 0; p < 2; ++p)
-      /* sites of one parity touch disjoint links (Sec. 2.2): a build with
-       * -fopenmp may visit them in parallel with the same result; the plain
-       * build ignores the pragma */
-#pragma omp parallel for schedule(static)
-      for (long s = 0; s < L.V; ++s) {
-        if (parity_of(&L, s) != p) continue;
-        if (slice_active && !slice_active[s / V3]) continue;
-        for (int sub = 0; sub < 3; ++sub) {
-          int n = 1;
-          double gap = INFINITY;
-          site_subgroup_update(dims, U, s, sub, gauge, algo, param,
-                               sweep0 + (uint32_t)k, seed, copy, &n, &gap);
-          if (trials) trials[s * 3 + sub] = n;
-          if (margin) margin[s * 3 + sub] = gap;
-        }
-      }
+      half_sweep(&L, dims, U, gauge, algo, param, p, sweep0 + (uint32_t)k,
+                 seed, copy, slice_active, trials, margin);
+}
+
+/* The sites of parity p only, with the draws of sweep index `sweep` (the
+ * half-sweeps of Alg. 1 one at a time, as a time-slab decomposition over
+ * several processes runs them, Sec. 5). */
+void or_half_sweep(const int dims[4], double* U, int gauge, int algo,
+                   double param, int parity, uint32_t sweep, uint64_t seed,
+                   uint32_t copy, const int* slice_active) {
+  lattice L = make_lattice(dims);
+  half_sweep(&L, dims, U, gauge, algo, param, parity & 1, sweep, seed, copy,
+             slice_active, NULL, NULL);
 }
 
 void or_sweep(const int dims[4], double* U, int gauge, int algo, double param,

@@ -83,8 +83,8 @@ int volume_class(uint64_t v) {
 }
 
 struct Layout {
-  size_t links32 = 0, links64 = 0, gscratch = 0, obs_site = 0, active = 0, partial = 0, obs = 0, err = 0,
-         staging = 0, total = 0;
+  size_t links32 = 0, links64 = 0, gscratch = 0, obs_site = 0, active = 0, slab = 0, partial = 0, obs = 0,
+         err = 0, staging = 0, total = 0;
   int slab_nt = 1;
 };
 
@@ -101,7 +101,7 @@ int check_dims(const int dims[4], int ncopies, int gauge, int prec) {
   if ((uint64_t)ncopies * dims[0] * 2 > 65535) return fail(GF_EINVAL, "n_copies * Nt * 2 must be <= 65535");
   if ((uint64_t)ncopies * V >= (1ull << 40)) return fail(GF_EINVAL, "batch too large");
   if (gauge < GF_LANDAU || gauge > GF_MAG) return fail(GF_EINVAL, "bad gauge %d", gauge);
-  if (prec < GF_FP64 || prec > GF_MIXED) return fail(GF_EINVAL, "bad precision %d", prec);
+  if (prec < GF_FP64 || prec > GF_MP) return fail(GF_EINVAL, "bad precision %d", prec);
   return GF_OK;
 }
 
@@ -129,18 +129,21 @@ Layout make_layout(const int dims[4], int ncopies, int gauge, int prec) {
   const int NS32 = (gauge == GF_COULOMB || prec == GF_MIXED) ? 5 : 4;
   const int NS64 = gauge == GF_COULOMB ? 5 : 4;
   if (prec != GF_FP64) L.links32 = round_up((size_t)ncopies * 2 * NS32 * G.Vh * 3 * sizeof(float4));
-  if (prec != GF_FP32) L.links64 = round_up((size_t)ncopies * 2 * NS64 * G.Vh * 6 * sizeof(double2));
+  if (prec == GF_FP64 || prec == GF_MIXED)
+    L.links64 = round_up((size_t)ncopies * 2 * NS64 * G.Vh * 6 * sizeof(double2));
   // GF_MIXED: the re-unitarised FP64 accumulator, full 3x3, used by the master sync
   if (prec == GF_MIXED) L.gscratch = round_up((size_t)ncopies * 2 * G.Vh * 9 * sizeof(double2));
   L.obs_site = round_up((size_t)ncopies * G.V * sizeof(double2));  // fused per-site F/theta
   L.active = round_up((size_t)ncopies * dims[0] * sizeof(int));
+  L.slab = round_up((size_t)3 * dims[0] * sizeof(int));  // time-slab slice masks (all / boundary / inner)
   L.partial = round_up(gfk::observables_partial_doubles(G, ncopies) * sizeof(double));
   L.obs = round_up((size_t)ncopies * dims[0] * 2 * sizeof(double));
   L.err = ALIGN;  // the sweep kernels' error word
   const size_t slice_bytes = (size_t)G.V3 * 4 * 18 * sizeof(double);
   L.slab_nt = (int)std::max<size_t>(1, std::min<size_t>(dims[0], STAGING_BYTES / slice_bytes));
   L.staging = round_up((size_t)L.slab_nt * slice_bytes);
-  L.total = L.links32 + L.links64 + L.gscratch + L.obs_site + L.active + L.partial + L.obs + L.err + L.staging;
+  L.total = L.links32 + L.links64 + L.gscratch + L.obs_site + L.active + L.slab + L.partial + L.obs + L.err +
+            L.staging;
   return L;
 }
 
@@ -179,6 +182,13 @@ struct gf_ctx {
   int fused_obs = 1;       // F/theta fused into the last OR sweep where possible
   int sa_micro = 3;        // microcanonical sweeps after each heat-bath sweep (Sec. 2.3)
   int* sa_trace_d = nullptr;  // caller's device buffer for heat-bath trial counts, or nullptr
+  // time-slab mode (Sec. 5): local slice 0 is a halo copy of global slice t0-1,
+  // slices 1..Nt-2 are owned (global t0 ..), slice Nt-1 an unused pad
+  bool slab = false;
+  int slab_t0 = 0, slab_Nt = 0;
+  int parity_flip = 0;        // local parity = global parity ^ parity_flip
+  uint32_t site_offset = 0;   // global site index = local index + site_offset (Philox counters)
+  int* slab_flags_d = nullptr;  // 3 x Nt flags: owned, boundary (first/last owned), inner
   int lpt[2][5] = {{0}};  // [fp64][algo] chosen links per thread, 0 = default
   int pmode[2][5] = {{0}};  // [fp64][algo] tile fetch chosen by gf_autotune + 1, 0 = the context's
   // optional per-kernel timing: CUDA events around every launch of a class
@@ -258,7 +268,7 @@ int default_lpt(const gf_ctx* c, int algo) {
 }
 
 int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, uint32_t sweep, int lpt,
-                int obs = 0, int update = 1, int pmode = -1) {
+                int obs = 0, int update = 1, int pmode = -1, const int* active_override = nullptr) {
   const int prefetch = pmode >= 0 ? pmode : c->prefetch;
   cudaError_t e;
   if (c->fp64) {
@@ -282,6 +292,8 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     a.err = c->err_d;
     a.wait_polls = -1;
     a.sa_trace = kalgo == gfk::ALG_SA ? c->sa_trace_d : nullptr;
+    a.site_offset = c->site_offset;
+    if (active_override) a.active = active_override;
     cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<double>(a, c->gauge, kalgo, lpt, c->st);
     prof_end(c, t0, GF_KERNEL_SWEEP_FP64);
@@ -307,9 +319,12 @@ int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, u
     a.err = c->err_d;
     a.wait_polls = c->stage_wait_polls;
     a.sa_trace = kalgo == gfk::ALG_SA ? c->sa_trace_d : nullptr;
+    a.site_offset = c->site_offset;
+    if (active_override) a.active = active_override;
     if (a.prefetch == GF_PREFETCH_SMEM) c->err_pending = true;
     cudaEvent_t t0 = prof_begin(c);
-    e = gfk::launch_sweep<float>(a, c->gauge, kalgo, lpt, c->st);
+    e = c->prec == GF_MP ? gfk::launch_sweep_mp(a, c->gauge, kalgo, lpt, c->st)
+                         : gfk::launch_sweep<float>(a, c->gauge, kalgo, lpt, c->st);
     prof_end(c, t0, GF_KERNEL_SWEEP_FP32);
     c->launch_count++;
   }
@@ -585,6 +600,7 @@ int create_impl(const int dims[4], int ncopies, int gauge, int prec, void* strea
   if (L.gscratch) { c->gscratch = base + off; off += L.gscratch; }
   c->obs_site = base + off; off += L.obs_site;
   c->active_d = reinterpret_cast<int*>(base + off); off += L.active;
+  c->slab_flags_d = reinterpret_cast<int*>(base + off); off += L.slab;
   c->partial = reinterpret_cast<double*>(base + off); off += L.partial;
   c->obs_d = reinterpret_cast<double*>(base + off); off += L.obs;
   c->err_d = reinterpret_cast<int*>(base + off); off += L.err;
@@ -617,6 +633,11 @@ int create_impl(const int dims[4], int ncopies, int gauge, int prec, void* strea
 }
 
 int check_ctx(gf_ctx* c) { return c ? GF_OK : fail(GF_EINVAL, "context is NULL"); }
+
+// Whole-lattice sweeps would update the halo slices of a time slab.
+int check_not_slab(gf_ctx* c, const char* what) {
+  return c->slab ? fail(GF_EINVAL, "%s: the context is a time slab; sweep it with gf_sweep_half", what) : GF_OK;
+}
 
 int check_copy(gf_ctx* c, int copy, bool allow_all) {
   if (copy == -1 && allow_all) return GF_OK;
@@ -868,6 +889,7 @@ int gf_store_links_device(gf_ctx* c, int copy, double* dev) {
 int gf_random_gauge_transform_async(gf_ctx* c, uint64_t seed) {
   int r = check_ctx(c);
   if (r) return r;
+  if ((r = check_not_slab(c, "gf_random_gauge_transform_async"))) return r;
   if ((r = consolidate(c))) return r;
   cudaError_t e = c->master64()
                       ? gfk::launch_haar_transform<double>(c->links64, c->G, c->NS64, c->ncopies, c->copy_base, seed, c->st)
@@ -887,6 +909,7 @@ int gf_random_gauge_transform(gf_ctx* c, uint64_t seed) {
 int gf_sweep_async(gf_ctx* c, gf_algo algo, double param, int n_sweeps, uint64_t seed) {
   int r = check_ctx(c);
   if (r) return r;
+  if ((r = check_not_slab(c, "gf_sweep_async"))) return r;
   if ((r = check_algo_param(algo, param))) return r;
   if (n_sweeps < 0) return fail(GF_EINVAL, "n_sweeps < 0");
   if (algo == GF_OR || algo == GF_RELAX) {
@@ -901,6 +924,7 @@ int gf_sweep_async(gf_ctx* c, gf_algo algo, double param, int n_sweeps, uint64_t
 int gf_anneal_async(gf_ctx* c, double T0, double T1, int n_steps, uint64_t seed) {
   int r = check_ctx(c);
   if (r) return r;
+  if ((r = check_not_slab(c, "gf_anneal_async"))) return r;
   if (!(T0 > 0) || !(T1 > 0) || !std::isfinite(T0) || !std::isfinite(T1))
     return fail(GF_EINVAL, "temperatures must be > 0");
   if (n_steps < 0) return fail(GF_EINVAL, "n_steps < 0");
@@ -922,13 +946,14 @@ int gf_synchronize(gf_ctx* c) {
 int gf_sweep(gf_ctx* c, gf_algo algo, double param, int n_sweeps, uint64_t seed, double* F, double* theta) {
   int r = check_ctx(c);
   if (r) return r;
+  if ((r = check_not_slab(c, "gf_sweep"))) return r;
   if ((r = check_algo_param(algo, param))) return r;
   if (n_sweeps < 0) return fail(GF_EINVAL, "n_sweeps < 0");
   // fused observables: the odd half of the last sweep writes F/theta of its
   // sites (only when those links are the final ones: not in the FP32 stage of
   // GF_MIXED, whose master is read instead)
   const bool fused = c->fused_obs && (F || theta) && n_sweeps > 0 && (algo == GF_OR || algo == GF_RELAX) &&
-                     !(c->prec == GF_MIXED && !c->fp64);
+                     !(c->prec == GF_MIXED && !c->fp64) && c->prec != GF_MP;
   if ((algo == GF_OR || algo == GF_RELAX) && n_sweeps > 0) {
     const double omega = algo == GF_RELAX ? 1.0 : param;
     if ((r = plain_sweeps(c, gfk::ALG_OR, algo, omega, n_sweeps - 1))) return r;
@@ -949,6 +974,7 @@ int gf_sweep(gf_ctx* c, gf_algo algo, double param, int n_sweeps, uint64_t seed,
 int gf_anneal(gf_ctx* c, double T0, double T1, int n_steps, uint64_t seed, double* F, double* theta) {
   int r = check_ctx(c);
   if (r) return r;
+  if ((r = check_not_slab(c, "gf_anneal"))) return r;
   if (!(T0 > 0) || !(T1 > 0) || !std::isfinite(T0) || !std::isfinite(T1))
     return fail(GF_EINVAL, "temperatures must be > 0");
   if (n_steps < 0) return fail(GF_EINVAL, "n_steps < 0");
@@ -1051,6 +1077,86 @@ int gf_set_sa_trace(gf_ctx* c, int* device_counts) {
   if (((uintptr_t)device_counts & 3) != 0) return fail(GF_EINVAL, "device_counts must be 4-byte aligned");
   c->sa_trace_d = device_counts;
   return GF_OK;
+}
+
+int gf_set_slab(gf_ctx* c, int t0, int Nt_global) {
+  int r = check_ctx(c);
+  if (r) return r;
+  const int nl = c->dims[0];
+  if (c->ncopies != 1) return fail(GF_EINVAL, "a time slab holds one lattice (n_copies = %d)", c->ncopies);
+  if (c->gauge == GF_COULOMB) return fail(GF_EINVAL, "Coulomb time-slices need no slab exchange: split them as units");
+  if (c->prec == GF_MIXED) return fail(GF_EINVAL, "time slabs run in GF_FP64 or GF_FP32 storage");
+  if (nl < 4) return fail(GF_EINVAL, "a slab needs at least two owned slices (local Nt = %d)", nl);
+  if (Nt_global < nl - 2 || (Nt_global & 1) || t0 < 0 || t0 >= Nt_global)
+    return fail(GF_EINVAL, "slab t0 = %d, Nt_global = %d do not fit %d owned slices", t0, Nt_global, nl - 2);
+  std::vector<int> flags((size_t)3 * nl, 0);
+  for (int t = 1; t <= nl - 2; ++t) {
+    flags[t] = 1;                                   // owned
+    flags[nl + t] = (t == 1 || t == nl - 2) ? 1 : 0;  // boundary: the first and last owned slice
+    flags[2 * nl + t] = 1 - flags[nl + t];          // inner
+  }
+  GF_CUDA(cudaMemcpyAsync(c->slab_flags_d, flags.data(), flags.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  GF_CUDA(cudaStreamSynchronize(c->st));
+  c->slab = true;
+  c->slab_t0 = t0;
+  c->slab_Nt = Nt_global;
+  c->parity_flip = (t0 - 1) & 1;
+  c->site_offset = (uint32_t)((int64_t)(t0 - 1) * (int64_t)c->G.V3);
+  return GF_OK;
+}
+
+int gf_sweep_half(gf_ctx* c, gf_algo algo, double param, int parity, int part, uint64_t seed) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if ((r = check_algo_param(algo, param))) return r;
+  if (parity != 0 && parity != 1) return fail(GF_EINVAL, "parity must be 0 or 1");
+  if (part < GF_SLAB_OWNED || part > GF_SLAB_INNER) return fail(GF_EINVAL, "bad part %d", part);
+  if (!c->slab && part != GF_SLAB_OWNED) return fail(GF_EINVAL, "boundary/inner parts need a time slab");
+  if (c->prec == GF_MIXED && !c->fp64) return fail(GF_EINVAL, "gf_sweep_half runs on FP64 or FP32 storage");
+  const int kalgo = algo == GF_MICRO ? gfk::ALG_MICRO : algo == GF_SR ? gfk::ALG_SR : algo == GF_SA ? gfk::ALG_SA
+                                                                                            : gfk::ALG_OR;
+  const double p = algo == GF_RELAX ? 1.0 : algo == GF_MICRO ? 0.0 : param;
+  const int* act = c->slab ? c->slab_flags_d + (size_t)part * c->dims[0] : nullptr;
+  const int pm = c->pmode[c->fp64][algo] - 1;
+  r = launch_half(c, kalgo, p, parity ^ c->parity_flip, seed, (uint32_t)c->sweep_index, default_lpt(c, algo), 0, 1,
+                  pm, act);
+  if (r) return r;
+  return GF_OK;
+}
+
+int gf_slab_bytes(gf_ctx* c, size_t* bytes) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!bytes) return fail(GF_EINVAL, "bytes is NULL");
+  *bytes = (size_t)(c->fp64 ? 6 : 3) * (c->G.V3 / 2) * 16;
+  return GF_OK;
+}
+
+// U_0 rows 0,1 of the sites of one parity in one local time-slice: NC chunks
+// of V3/2 vectors, contiguous per chunk in the storage (Sec. 5.2's argument
+// for a time-slice-major, parity-split layout), moved by one 2-D copy.
+static int slab_copy(gf_ctx* c, int slice, int parity, void* buf, bool pack) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!buf) return fail(GF_EINVAL, "buffer is NULL");
+  if (slice < 0 || slice >= c->dims[0]) return fail(GF_EINVAL, "slice %d outside [0,%d)", slice, c->dims[0]);
+  if (parity != 0 && parity != 1) return fail(GF_EINVAL, "parity must be 0 or 1");
+  if (c->prec == GF_MIXED && !c->fp64) return fail(GF_EINVAL, "slab exchange runs on FP64 or FP32 storage");
+  const int NC = c->fp64 ? 6 : 3;
+  const size_t half = c->G.V3 / 2;
+  const size_t elem = gfk::link_off(0, parity ^ c->parity_flip, 0, c->NS(), NC, c->G.Vh, (uint32_t)(slice * half));
+  char* links = static_cast<char*>(c->links()) + elem * 16;
+  const size_t pitch = (size_t)c->G.Vh * 16, width = half * 16;
+  cudaError_t e = pack ? cudaMemcpy2DAsync(buf, width, links, pitch, width, NC, cudaMemcpyDefault, c->st)
+                       : cudaMemcpy2DAsync(links, pitch, buf, width, width, NC, cudaMemcpyDefault, c->st);
+  if (e != cudaSuccess) return fail(GF_ECUDA, "slab %s: %s", pack ? "pack" : "unpack", cudaGetErrorString(e));
+  return GF_OK;
+}
+
+int gf_slab_pack(gf_ctx* c, int slice, int parity, void* buf) { return slab_copy(c, slice, parity, buf, true); }
+
+int gf_slab_unpack(gf_ctx* c, int slice, int parity, const void* buf) {
+  return slab_copy(c, slice, parity, const_cast<void*>(buf), false);
 }
 
 int gf_set_fused_observables(gf_ctx* c, int on) {
@@ -1188,6 +1294,7 @@ void log_check(gf_ctx* c, const char* call, int check, int sweeps, double worst,
 int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
   int r = check_ctx(c);
   if (r) return r;
+  if ((r = check_not_slab(c, "gf_fix"))) return r;
   if (!P) return fail(GF_EINVAL, "params is NULL");
   if (P->algo != GF_OR && P->algo != GF_RELAX) return fail(GF_EINVAL, "gf_fix runs GF_OR or GF_RELAX");
   if ((r = check_algo_param(P->algo, P->param))) return r;
@@ -1232,7 +1339,7 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
         unit_theta[k] = s / Nt;
       }
     }
-    const bool final_phase = c->fp64 || c->prec == GF_FP32;
+    const bool final_phase = c->fp64 || c->prec == GF_FP32 || c->prec == GF_MP;
     for (int k = 0; k < c->ncopies; ++k)
       for (int u = 0; u < units_per_copy; ++u) {
         const double th = unit_theta[(size_t)k * units_per_copy + u];
@@ -1305,8 +1412,10 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
       Range range_sweeps(c->fp64 ? "sweeps fp64" : "sweeps fp32");
       if ((r = plain_sweeps(c, kalgo, P->algo, omega, has_last ? seg - 1 : seg))) return r;
       if (has_last) {
-        if ((r = full_sweep(c, kalgo, P->algo, omega, 0, 0, true))) return r;
-        fused_ready = true;
+        // the MP kernels have no fused-observables variant: the check reads the links
+        const bool fuse = c->prec != GF_MP;
+        if ((r = full_sweep(c, kalgo, P->algo, omega, 0, 0, fuse))) return r;
+        fused_ready = fuse;
       }
       R.site_updates += (uint64_t)seg * n_active * sites_per_unit;
       if (c->fp64)
@@ -1337,6 +1446,7 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
 int gf_protocol(gf_ctx* c, const gf_protocol_params* P, gf_fix_result* res) {
   int r = check_ctx(c);
   if (r) return r;
+  if ((r = check_not_slab(c, "gf_protocol"))) return r;
   if (!P) return fail(GF_EINVAL, "params is NULL");
   if (P->sa_steps < 0 || P->sr_sweeps < 0) return fail(GF_EINVAL, "negative sweep counts");
   if (P->sa_steps > 0 && (!(P->T_start > 0) || !(P->T_end > 0))) return fail(GF_EINVAL, "temperatures must be > 0");

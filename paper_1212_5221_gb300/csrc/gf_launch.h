@@ -12,6 +12,8 @@ struct SweepArgs;
 // One half-sweep of the given gauge/algorithm with lpt links per thread.
 template <typename R>
 cudaError_t launch_sweep(const SweepArgs<R>& a, int gauge, int algo, int lpt, cudaStream_t st);
+// FP32 storage with Step 1 in FP64 (GF_MP).
+cudaError_t launch_sweep_mp(const SweepArgs<float>& a, int gauge, int algo, int lpt, cudaStream_t st);
 
 // Exact F/theta per (copy, slice) into out[ct][2] (device).
 template <typename R>

@@ -1,6 +1,8 @@
 // gf_sweep.cuh -- the checkerboard sweep kernel (Alg. 1, one sublattice per
 // launch) and the helpers it shares with the auxiliary kernels.
 #pragma once
+#include <type_traits>
+
 #include "gf_device.cuh"
 
 namespace gfk {
@@ -32,6 +34,8 @@ struct SweepArgs {
                       // (2^24, about 2 s), 0 none (the wait runs out at once)
   int* sa_trace;      // heat bath only, or nullptr: [copy][site][subgroup] Kennedy-Pendleton
                       // trial counts (0 = none accepted; MAG: 1), written by lane 0
+  uint32_t site_offset;  // added to the site index in the Philox counters (time slabs: the
+                         // global index of a local site)
 };
 
 // Per-site FP64 observables of the MAG form from the slot matrices M
@@ -100,8 +104,8 @@ __device__ __forceinline__ void site_observables_mag(const mat3<R> (&u)[LPT], co
 }
 
 // Element offset of (copy, parity, slot, chunk 0, site index).
-__device__ __forceinline__ size_t link_off(uint32_t copy, int p, int slot, int NS, int NC, uint32_t Vh,
-                                           uint32_t sp) {
+__host__ __device__ __forceinline__ size_t link_off(uint32_t copy, int p, int slot, int NS, int NC, uint32_t Vh,
+                                                    uint32_t sp) {
   return ((((size_t)copy * 2 + p) * NS + slot) * NC) * Vh + sp;
 }
 
@@ -345,9 +349,11 @@ __device__ __forceinline__ void load_slot(const float4* stage, const Geom& G, ui
 // which gives bit-identical sums in all lanes, so all lanes compute the same
 // g (Step 1) and apply it to their own slots (Step 2).  The grid is
 // persistent over tiles of BLOCK/L sites.
-template <typename R, int ALGO, int LPT, bool OBS>
+template <typename R, int ALGO, int LPT, bool OBS, bool MP>
 __device__ __forceinline__ void sweep_site_mag(const SweepArgs<R>& a, uint32_t copy, uint32_t sp, bool valid,
                                                int lane, const float4* stage, uint32_t sp0) {
+  // S: the precision Step 1 runs in (FP64 for the MP variant of FP32 storage)
+  using S = typename std::conditional<MP, double, R>::type;
   constexpr uint32_t TILE = BLOCK / (8 / LPT);
   constexpr int NC = store_traits<R>::NC;
   constexpr int L = 8 / LPT;
@@ -413,7 +419,7 @@ __device__ __forceinline__ void sweep_site_mag(const SweepArgs<R>& a, uint32_t c
     }
   }
 
-  Rng rng{a.k0, a.k1, s, a.sweep, a.copy0 + copy};
+  Rng rng{a.k0, a.k1, s + a.site_offset, a.sweep, a.copy0 + copy};
 
   if (OBS && a.obs == 1) {  // theta of the current links at this site
     double F, th;
@@ -427,15 +433,16 @@ __device__ __forceinline__ void sweep_site_mag(const SweepArgs<R>& a, uint32_t c
     const int i = sub == 2 ? 1 : 0;
     const int j2 = sub == 0 ? 1 : 2;
     // x = Pauli vector of sum W s3 W^dag over the slots' (i,j) blocks
-    R x1 = 0, x2 = 0, x3 = 0;
+    S x1 = 0, x2 = 0, x3 = 0;
 #pragma unroll
     for (int j = 0; j < LPT; ++j) {
       if (!use[j]) continue;
-      cx<R> A = u[j].e[i][i], B = u[j].e[i][j2], C = u[j].e[j2][i], D = u[j].e[j2][j2];
-      cx<R> x01 = cmul2c(A, C, cx<R>{-B.re, -B.im}, D);  // A conj(C) - B conj(D)
+      const cx<S> A{(S)u[j].e[i][i].re, (S)u[j].e[i][i].im}, B{(S)u[j].e[i][j2].re, (S)u[j].e[i][j2].im};
+      const cx<S> C{(S)u[j].e[j2][i].re, (S)u[j].e[j2][i].im}, D{(S)u[j].e[j2][j2].re, (S)u[j].e[j2][j2].im};
+      cx<S> x01 = cmul2c(A, C, cx<S>{-B.re, -B.im}, D);  // A conj(C) - B conj(D)
       x1 += x01.re;
       x2 -= x01.im;
-      x3 += R(0.5) * ((A.re * A.re + A.im * A.im) - (B.re * B.re + B.im * B.im) -
+      x3 += S(0.5) * ((A.re * A.re + A.im * A.im) - (B.re * B.re + B.im * B.im) -
                       (C.re * C.re + C.im * C.im) + (D.re * D.re + D.im * D.im));
     }
 #pragma unroll
@@ -444,19 +451,20 @@ __device__ __forceinline__ void sweep_site_mag(const SweepArgs<R>& a, uint32_t c
       x2 += __shfl_xor_sync(FULL, x2, o);
       x3 += __shfl_xor_sync(FULL, x3, o);
     }
-    R r;
-    quat<R> m = mag_max(x1, x2, x3, r);
-    quat<R> g;
-    if (ALGO == ALG_OR) g = rule_or(m, a.param);
-    else if (ALGO == ALG_MICRO) g = mag_micro(x1, x2, x3, r);
+    S r;
+    quat<S> m = mag_max(x1, x2, x3, r);
+    quat<S> gs;
+    if (ALGO == ALG_OR) gs = rule_or(m, (S)a.param);
+    else if (ALGO == ALG_MICRO) gs = mag_micro(x1, x2, x3, r);
     else if (ALGO == ALG_SR) {
       double ua, ub;
       rng.draw2(TAG_SR, (uint32_t)sub, 0, ua, ub);
-      g = ((R)ua < a.param) ? mag_micro(x1, x2, x3, r) : rule_or(m, R(1));
+      gs = ((S)ua < (S)a.param) ? mag_micro(x1, x2, x3, r) : rule_or(m, S(1));
     } else {
-      g = rule_sa_mag(m, r, a.param, rng, (uint32_t)sub);
+      gs = rule_sa_mag(m, r, (S)a.param, rng, (uint32_t)sub);
       if (a.sa_trace && valid && lane == 0) a.sa_trace[((size_t)copy * G.V + s) * 3 + sub] = 1;
     }
+    const quat<R> g{(R)gs.q0, (R)gs.q1, (R)gs.q2, (R)gs.q3};
 #pragma unroll
     for (int j = 0; j < LPT; ++j) left_subgroup_mult(u[j], i, j2, g);
     if (acc) left_subgroup_mult(gacc, i, j2, g);
@@ -594,9 +602,30 @@ __device__ __forceinline__ void apply_right_dag(const mat3<R>& G, const mat3<R>&
     }
 }
 
-template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
+// K (in FP64) += the slot's matrix from its stored rows (row 2 rebuilt in FP64).
+template <typename R>
+__device__ __forceinline__ void add_stored_k64(const mat3<R>& rows, bool down, mat3<double>& K) {
+  mat3<double> d;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) d.e[a][b] = {(double)rows.e[a][b].re, (double)rows.e[a][b].im};
+  reconstruct_row2(d);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      K.e[a][b].re += down ? d.e[b][a].re : d.e[a][b].re;
+      K.e[a][b].im += down ? -d.e[b][a].im : d.e[a][b].im;
+    }
+}
+
+template <typename R, int GAUGE, int ALGO, int LPT, bool OBS, bool MP>
 __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t copy, uint32_t sp, bool valid,
                                              int lane, const float4* stage, uint32_t sp0) {
+  // S: the precision of Step 1 (the gathered K, the subgroup choices and G);
+  // the MP variant of FP32 storage (Sec. 4.5) runs it in FP64, Step 2 in FP32
+  using S = typename std::conditional<MP, double, R>::type;
   constexpr uint32_t TILE = BLOCK / (8 / LPT);
   constexpr int NC = store_traits<R>::NC;
   constexpr int L = 8 / LPT;
@@ -644,11 +673,11 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
 
   // gather: K = sum of U_mu(x) and U_mu(x - mu)^dag over the lane's slots
   mat3<R> u[KEEP ? LPT : 1];
-  mat3<R> K;
+  mat3<S> K;
 #pragma unroll
   for (int x = 0; x < 3; ++x)
 #pragma unroll
-    for (int y = 0; y < 3; ++y) K.e[x][y] = {R(0), R(0)};
+    for (int y = 0; y < 3; ++y) K.e[x][y] = {S(0), S(0)};
   constexpr bool OBS_FP64 = OBS && sizeof(R) == 4;  // FP32 kernels gather the FP64 K separately
   double kr[3][3], ki[3][3];
   if (OBS) {
@@ -669,15 +698,19 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
     if (KEEP) u[KEEP ? j : 0] = t;
     if (use[j] && gather[j]) {
       if (OBS_FP64 && a.obs == 1) add_stored_fp64(t, dn[j], kr, ki);
-      reconstruct_row2(t);
+      if constexpr (MP) {
+        add_stored_k64(t, dn[j], K);
+      } else {
+        reconstruct_row2(t);
 #pragma unroll
-      for (int x = 0; x < 3; ++x)
+        for (int x = 0; x < 3; ++x)
 #pragma unroll
-        for (int y = 0; y < 3; ++y) {
-          const cx<R> v = dn[j] ? cx<R>{t.e[y][x].re, -t.e[y][x].im} : t.e[x][y];
-          K.e[x][y].re += v.re;
-          K.e[x][y].im += v.im;
-        }
+          for (int y = 0; y < 3; ++y) {
+            const cx<R> v = dn[j] ? cx<R>{t.e[y][x].re, -t.e[y][x].im} : t.e[x][y];
+            K.e[x][y].re += v.re;
+            K.e[x][y].im += v.im;
+          }
+      }
     }
   }
 #pragma unroll
@@ -707,12 +740,13 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
   if (OBS && !a.update) return;
 
   // Step 1: the three subgroups in the order (0,1), (0,2), (1,2)
-  Rng rng{a.k0, a.k1, s, a.sweep, a.copy0 + copy};
+  Rng rng{a.k0, a.k1, s + a.site_offset, a.sweep, a.copy0 + copy};
   int* trace = (ALGO == ALG_SA && a.sa_trace && valid && lane == 0) ? a.sa_trace + ((size_t)copy * Gm.V + s) * 3
                                                                      : nullptr;
-  const su2m<R> h0 = su2_of(choose_k<R, ALGO>(K.e[0][0], K.e[0][1], K.e[1][0], K.e[1][1], a.param, rng, 0u, trace));
+  const S prm = (S)a.param;
+  const su2m<S> h0 = su2_of(choose_k<S, ALGO>(K.e[0][0], K.e[0][1], K.e[1][0], K.e[1][1], prm, rng, 0u, trace));
   {  // K <- g0 K on the entries read later: row 0, and row 1 columns 1, 2
-    cx<R> r0[3];
+    cx<S> r0[3];
 #pragma unroll
     for (int y = 0; y < 3; ++y) r0[y] = cmul2(h0.h00, K.e[0][y], h0.h01, K.e[1][y]);
 #pragma unroll
@@ -720,17 +754,18 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
 #pragma unroll
     for (int y = 0; y < 3; ++y) K.e[0][y] = r0[y];
   }
-  const su2m<R> h1 = su2_of(choose_k<R, ALGO>(K.e[0][0], K.e[0][2], K.e[2][0], K.e[2][2], a.param, rng, 1u, trace));
+  const su2m<S> h1 = su2_of(choose_k<S, ALGO>(K.e[0][0], K.e[0][2], K.e[2][0], K.e[2][2], prm, rng, 1u, trace));
 #pragma unroll
   for (int y = 1; y < 3; ++y) K.e[2][y] = cmul2(h1.h10, K.e[0][y], h1.h11, K.e[2][y]);  // row 2 of g1 K
-  const su2m<R> h2 = su2_of(choose_k<R, ALGO>(K.e[1][1], K.e[1][2], K.e[2][1], K.e[2][2], a.param, rng, 2u, trace));
+  const su2m<S> h2 = su2_of(choose_k<S, ALGO>(K.e[1][1], K.e[1][2], K.e[2][1], K.e[2][2], prm, rng, 2u, trace));
 
   // G = g2 g1 g0 in the 3x3 embedding
-  mat3<R> G;
+  mat3<S> Gs;
   {
+    mat3<S>& G = Gs;
     // g1 g0: rows 0 and 2 mixed, row 1 = row 1 of g0
-    const cx<R> r00 = cmul(h1.h00, h0.h00), r01 = cmul(h1.h00, h0.h01);
-    const cx<R> r20 = cmul(h1.h10, h0.h00), r21 = cmul(h1.h10, h0.h01);
+    const cx<S> r00 = cmul(h1.h00, h0.h00), r01 = cmul(h1.h00, h0.h01);
+    const cx<S> r20 = cmul(h1.h10, h0.h00), r21 = cmul(h1.h10, h0.h01);
     G.e[0][0] = r00;
     G.e[0][1] = r01;
     G.e[0][2] = h1.h01;
@@ -742,6 +777,12 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
     G.e[2][1] = cmul2(h2.h10, h0.h11, h2.h11, r21);
     G.e[2][2] = cmul(h2.h11, h1.h11);
   }
+  // Step 2 runs in the storage precision
+  mat3<R> G;
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+#pragma unroll
+    for (int y = 0; y < 3; ++y) G.e[x][y] = {(R)Gs.e[x][y].re, (R)Gs.e[x][y].im};
 
   // mixed precision: the site's accumulated gauge transformation (FP32 working copy only)
   constexpr bool CAN_ACC = sizeof(R) == 4 && GAUGE != COULOMB;
@@ -796,19 +837,20 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
 // the per-slot MAG form 1 / 1 / 2 / 3.  (Reading the links again in FP32 as
 // well, to fit one more block, measured slower: 0.347 against 0.324 ms per
 // 32^3 x 64 sweep.)
-template <typename R, int GAUGE, int LPT>
+template <typename R, int GAUGE, int LPT, bool MP = false>
 constexpr int min_blocks() {
+  if (MP) return LPT == 8 ? 1 : LPT == 4 ? 1 : LPT == 2 ? 2 : 3;  // FP64 K and G in registers
   if (sizeof(R) == 4) return LPT == 8 ? 1 : LPT == 4 ? 2 : LPT == 2 ? 3 : 4;
   return GAUGE == MAG ? (LPT >= 4 ? 1 : LPT == 2 ? 2 : 3) : (LPT == 8 ? 2 : LPT >= 2 ? 1 : 2);
 }
 
-template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
+template <typename R, int GAUGE, int ALGO, int LPT, bool OBS, bool MP>
 __device__ __forceinline__ void site_dispatch(const SweepArgs<R>& a, uint32_t copy, uint32_t sp, bool valid, int lane,
                                               const float4* stage, uint32_t sp0) {
   if constexpr (GAUGE == MAG)
-    sweep_site_mag<R, ALGO, LPT, OBS>(a, copy, sp, valid, lane, stage, sp0);
+    sweep_site_mag<R, ALGO, LPT, OBS, MP>(a, copy, sp, valid, lane, stage, sp0);
   else
-    sweep_site_k<R, GAUGE, ALGO, LPT, OBS>(a, copy, sp, valid, lane, stage, sp0);
+    sweep_site_k<R, GAUGE, ALGO, LPT, OBS, MP>(a, copy, sp, valid, lane, stage, sp0);
 }
 
 // Persistent loop with two stage buffers (FP32, prefetch mode 2).  Warp 0
@@ -816,7 +858,7 @@ __device__ __forceinline__ void site_dispatch(const SweepArgs<R>& a, uint32_t co
 // __syncthreads at the end of an iteration frees the buffer that the next
 // iteration refills.  If a wait runs out, the block records the error, waits
 // (bounded) for the copies it issued and returns.
-template <int GAUGE, int ALGO, int LPT, bool OBS>
+template <int GAUGE, int ALGO, int LPT, bool OBS, bool MP>
 __device__ __forceinline__ void sweep_staged(const SweepArgs<float>& a) {
   constexpr int L = 8 / LPT;
   constexpr uint32_t TILE = BLOCK / L;
@@ -873,18 +915,19 @@ __device__ __forceinline__ void sweep_staged(const SweepArgs<float>& a) {
     const uint32_t copy = (uint32_t)(tile / tiles_per_copy);
     const uint32_t sp0 = (uint32_t)(tile - (uint64_t)copy * tiles_per_copy) * TILE;
     const uint32_t sp = sp0 + local;
-    site_dispatch<float, GAUGE, ALGO, LPT, OBS>(a, copy, sp, sp < Vh, lane, buf[b], sp0);
+    site_dispatch<float, GAUGE, ALGO, LPT, OBS, MP>(a, copy, sp, sp < Vh, lane, buf[b], sp0);
     __syncthreads();
   }
 }
 
 // OBS: the variant with the fused observables (used for overrelaxation check
-// sweeps only, so that the plain kernels keep their register budget).
-template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
-__global__ void __launch_bounds__(BLOCK, min_blocks<R, GAUGE, LPT>()) sweep_kernel(const SweepArgs<R> a) {
+// sweeps only, so that the plain kernels keep their register budget).  MP:
+// FP32 storage with Step 1 in FP64 (the paper's mixed-precision variant).
+template <typename R, int GAUGE, int ALGO, int LPT, bool OBS, bool MP = false>
+__global__ void __launch_bounds__(BLOCK, min_blocks<R, GAUGE, LPT, MP>()) sweep_kernel(const SweepArgs<R> a) {
   if constexpr (sizeof(R) == 4) {
     if (a.prefetch == 2) {
-      sweep_staged<GAUGE, ALGO, LPT, OBS>(a);
+      sweep_staged<GAUGE, ALGO, LPT, OBS, MP>(a);
       return;
     }
   }
@@ -905,7 +948,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R, GAUGE, LPT>()) sweep_kern
     }
     const uint32_t copy = (uint32_t)(tile / tiles_per_copy);
     const uint32_t sp0 = (uint32_t)(tile - (uint64_t)copy * tiles_per_copy) * TILE;
-    site_dispatch<R, GAUGE, ALGO, LPT, OBS>(a, copy, sp0 + local, sp0 + local < Vh, lane, nullptr, sp0);
+    site_dispatch<R, GAUGE, ALGO, LPT, OBS, MP>(a, copy, sp0 + local, sp0 + local < Vh, lane, nullptr, sp0);
   }
 }
 

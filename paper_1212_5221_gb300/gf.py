@@ -21,13 +21,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgf.so")
 
 GF_LANDAU, GF_COULOMB, GF_MAG = 0, 1, 2
-GF_FP64, GF_FP32, GF_MIXED = 0, 1, 2
+GF_FP64, GF_FP32, GF_MIXED, GF_MP = 0, 1, 2, 3
 GF_RELAX, GF_OR, GF_MICRO, GF_SR, GF_SA = 0, 1, 2, 3, 4
 GF_KERNEL_SWEEP_FP32, GF_KERNEL_SWEEP_FP64, GF_KERNEL_OBSERVABLES, GF_KERNEL_REUNITARIZE, GF_KERNEL_OTHER = range(5)
 GF_OK, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_ETIMEOUT, GF_ENOTCONV, GF_ENOSYS, GF_ECANCELED = range(8)
 
 GAUGES = {"landau": GF_LANDAU, "coulomb": GF_COULOMB, "mag": GF_MAG}
-PRECISIONS = {"fp64": GF_FP64, "fp32": GF_FP32, "mixed": GF_MIXED}
+PRECISIONS = {"fp64": GF_FP64, "fp32": GF_FP32, "mixed": GF_MIXED, "mp": GF_MP}
 ALGOS = {"relax": GF_RELAX, "or": GF_OR, "micro": GF_MICRO, "sr": GF_SR, "sa": GF_SA}
 
 
@@ -115,6 +115,11 @@ _SIG = {
     "gf_set_fused_observables": [_P, _I],
     "gf_set_sa_micro": [_P, _I],
     "gf_set_sa_trace": [_P, _P],
+    "gf_set_slab": [_P, _I, _I],
+    "gf_sweep_half": [_P, _I, ctypes.c_double, _I, _I, ctypes.c_uint64],
+    "gf_slab_bytes": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "gf_slab_pack": [_P, _I, _I, _P],
+    "gf_slab_unpack": [_P, _I, _I, _P],
     "gf_get_links_per_thread": [_P, _PI],
     "gf_autotune": [_P, _I, _PI, _PD],
     "gf_fix": [_P, ctypes.POINTER(gf_fix_params), ctypes.POINTER(gf_fix_result)],
@@ -385,6 +390,34 @@ def gf_set_sa_trace(h, device_ptr):
     """Record heat-bath trial counts into int32 device memory of n_copies*V*3
     entries ([copy][site][subgroup]); 0 or None turns the record off."""
     _check(lib().gf_set_sa_trace(h, ctypes.c_void_p(int(device_ptr) if device_ptr else 0)), "gf_set_sa_trace")
+
+
+GF_SLAB_OWNED, GF_SLAB_BOUNDARY, GF_SLAB_INNER = 0, 1, 2
+
+
+def gf_set_slab(h, t0, Nt_global):
+    """Make the context the time slab owning global slices [t0, t0 + local Nt - 2)."""
+    _check(lib().gf_set_slab(h, int(t0), int(Nt_global)), "gf_set_slab")
+
+
+def gf_sweep_half(h, algo, param, parity, part=GF_SLAB_OWNED, seed=0):
+    """One half-sweep of the sites of (global) parity `parity`, enqueued on the context's stream."""
+    _check(lib().gf_sweep_half(h, _enum(algo, ALGOS), float(param), int(parity), int(part),
+                               int(seed) & (2**64 - 1)), "gf_sweep_half")
+
+
+def gf_slab_bytes(h):
+    v = ctypes.c_size_t()
+    _check(lib().gf_slab_bytes(h, ctypes.byref(v)), "gf_slab_bytes")
+    return v.value
+
+
+def gf_slab_pack(h, slice_, parity, buf_ptr: int):
+    _check(lib().gf_slab_pack(h, int(slice_), int(parity), ctypes.c_void_p(int(buf_ptr))), "gf_slab_pack")
+
+
+def gf_slab_unpack(h, slice_, parity, buf_ptr: int):
+    _check(lib().gf_slab_unpack(h, int(slice_), int(parity), ctypes.c_void_p(int(buf_ptr))), "gf_slab_unpack")
 
 
 def gf_get_links_per_thread(h):
