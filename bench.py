@@ -350,10 +350,10 @@ def run_ours(args, rank, world, local_rank):
 
     out = {}
     if rank == 0:
-        def one_run(prec, switch):
+        def one_run(prec, switch, orbit_seed):
             fld = gf.GaugeField(dims, W["gauge"], prec, device=dev)
             gf.gf_load_links_device(fld.h, 0, src.data_ptr())
-            gf.gf_random_gauge_transform(fld.h, 1000)
+            gf.gf_random_gauge_transform(fld.h, orbit_seed)
             kw = dict(fix_kw, switch_theta=switch)
             r = gf.gf_fix(fld.h, **kw)
             F, T = gf.gf_functional_theta(fld.h)
@@ -362,31 +362,47 @@ def run_ours(args, rank, world, local_rank):
                     "sweeps_fp64": r["sweeps_fp64"], "site_updates_per_s": r["site_updates"] / r["seconds"],
                     "F": float(F[0]), "theta": float(T[0])}
 
-        # the same problem (orbit seed 1000) as plain FP64, and in mixed precision with the
-        # switch to FP64 sweeps moved down to the FP32 floor (one run each, outside the steps)
-        fp64 = one_run("fp64", args.switch_theta) if args.fp64_baseline else None
-        deep = one_run("mixed", args.deep_switch) if args.deep_switch > 0 else None
-        literal = one_run("mixed", args.switch_theta) if args.fp64_baseline else None
-        # end to end through the C ABI with pinned host buffers
+        # plain FP64 on the same problems as the first timed steps (orbit seeds 1000 + k),
+        # so that the two arms' time to theta compare like with like; and mixed precision
+        # with the switch to FP64 sweeps moved down to the FP32 floor (seed 1000)
+        n_match = min(args.fp64_matched, args.steps) if args.fp64_baseline else 0
+        fp64_runs = []
+        for k in range(n_match):
+            r64 = one_run("fp64", args.switch_theta, 1000 + k)
+            r64["mixed_seconds"] = results[k]["seconds"]
+            r64["mixed_sweeps"] = results[k]["sweeps"]
+            r64["rel_dF_mixed_vs_fp64"] = abs(results[k]["F_mean"] - r64["F"]) / abs(r64["F"])
+            fp64_runs.append(r64)
+            log(f"FP64 arm, orbit seed {1000 + k}: {r64['seconds']:.2f} s ({r64['sweeps']} sweeps); "
+                f"mixed {results[k]['seconds']:.2f} s ({results[k]['sweeps']} sweeps)")
+        fp64 = fp64_runs[0] if fp64_runs else None
+        deep = one_run("mixed", args.deep_switch, 1000) if args.deep_switch > 0 else None
+        # end to end through the C ABI with pinned host buffers, on the same orbit seeds as
+        # the first timed steps
         e2e = None
         if args.e2e_steps > 0:
             host_in = torch.from_numpy(U.view(np.float64).reshape(-1)).pin_memory()
             host_out = torch.empty_like(host_in).pin_memory()
             hin = host_in.numpy().view(np.complex128).reshape(U.shape)
             hout = host_out.numpy().view(np.complex128).reshape(U.shape)
+            n_e2e = min(args.e2e_steps, args.steps)
             torch.cuda.synchronize()
             t0 = time.time()
             su_e = 0
-            for k in range(args.e2e_steps):
+            for k in range(n_e2e):
                 gf.gf_load_links(h, 0, hin)
                 gf.gf_random_gauge_transform(h, 1000 + k)
                 r = gf.gf_fix(h, **fix_kw)
                 gf.gf_store_links(h, 0, hout)
                 su_e += r["site_updates"]
             te = time.time() - t0
+            su_dev = sum(results[k]["site_updates"] for k in range(n_e2e))
+            t_dev = sum(results[k]["seconds"] for k in range(n_e2e))
             e2e = {"value": su_e / te, "unit": "site-updates/s", "h2d_bytes_per_step": int(U.nbytes),
-                   "d2h_bytes_per_step": int(U.nbytes), "steps": args.e2e_steps,
-                   "seconds_per_step": te / args.e2e_steps}
+                   "d2h_bytes_per_step": int(U.nbytes), "steps": n_e2e,
+                   "orbit_seeds": [1000 + k for k in range(n_e2e)],
+                   "seconds_per_step": te / n_e2e,
+                   "same_steps_resident": {"value": su_dev / t_dev, "seconds_per_step": t_dev / n_e2e}}
         # the oracle on all host cores (OpenMP build), with the single-thread figure beside it
         cpu = None
         if args.cpu_seconds > 0:
@@ -416,15 +432,18 @@ def run_ours(args, rank, world, local_rank):
                        "check_interval": W["check"], "field": f"exp(i 0.35 H), seed {W['field_seed']}, "
                        "then Haar g(x) per step", "l2": "inputs larger than L2 (403 MB FP32 links)",
                        "parallelism": f"replicas x{world}"},
-            "time_to_theta_s": {"mixed": mixed_tt, "fp64": fp64["seconds"] if fp64 else None,
-                                "speedup_mixed_vs_fp64": (fp64["seconds"] / mixed_tt) if fp64 else None,
-                                "mixed_deep_switch": deep["seconds"] if deep else None,
-                                "speedup_mixed_deep_vs_fp64": (fp64["seconds"] / deep["seconds"])
-                                if (fp64 and deep) else None},
-            "same_orbit_runs": {"fp64": fp64, "mixed_switch_1e-8": literal,
-                                f"mixed_switch_{args.deep_switch:g}": deep,
-                                "rel_dF_mixed_vs_fp64": abs(literal["F"] - fp64["F"]) / fp64["F"]
-                                if (fp64 and literal) else None,
+            "time_to_theta_s": {
+                "mixed": mixed_tt,
+                "matched_orbit_seeds": [1000 + k for k in range(n_match)],
+                "mixed_matched": (float(np.mean([r["mixed_seconds"] for r in fp64_runs]))
+                                  if fp64_runs else None),
+                "fp64_matched": float(np.mean([r["seconds"] for r in fp64_runs])) if fp64_runs else None,
+                "speedup_mixed_vs_fp64": (float(np.mean([r["seconds"] for r in fp64_runs]) /
+                                                np.mean([r["mixed_seconds"] for r in fp64_runs]))
+                                          if fp64_runs else None),
+                "mixed_deep_switch": deep["seconds"] if deep else None,
+                "speedup_mixed_deep_vs_fp64": (fp64["seconds"] / deep["seconds"]) if (fp64 and deep) else None},
+            "same_orbit_runs": {"fp64": fp64_runs, f"mixed_switch_{args.deep_switch:g}": deep,
                                 "rel_dF_deep_vs_fp64": abs(deep["F"] - fp64["F"]) / fp64["F"]
                                 if (fp64 and deep) else None},
             "sweeps_per_step": {"fp32": sweeps32 / args.steps, "fp64": sweeps64 / args.steps},
@@ -702,6 +721,81 @@ def run_fullsize_study(args):
     print(json.dumps({"study": "fullsize", **out}), flush=True)
 
 
+def run_config3_study(args):
+    """The 64^3 x 256 lattice fixed as stated (eps = 0.3, seed 2, Haar g seed
+    2): Coulomb gauge as 256 time-slices in every launch (each slice stops on
+    its own) and Landau gauge, both GF_MIXED with the switch to FP64 sweeps at
+    theta < 1e-8 and the FP64 sweeps continuing to theta < 1e-12; per-check
+    JSON lines go to gpurun_out/ when that folder exists."""
+    import torch
+
+    from paper_1212_5221_gb300 import build, gf, inputs
+
+    build.build_all()
+    dims = (256, 64, 64, 64)
+    per_t = 64 ** 3 * 4 * 18
+    dev = torch.device("cuda", 0)
+    src = torch.empty(dims[0] * per_t, dtype=torch.float64, device=dev)
+    for t0 in range(0, dims[0], 16):
+        slab = inputs.links(dims, "smooth", 0.3, 2, t0=t0, nt=16)
+        src[t0 * per_t:(t0 + 16) * per_t].copy_(torch.from_numpy(slab.view(np.float64).reshape(-1)))
+    torch.cuda.synchronize()
+    out = {"lattice": "64^3x256", "switch_theta": 1e-8, "theta_target": 1e-12}
+    logdir = os.path.join(ROOT, "gpurun_out")
+    for gauge, omega, cap in (("coulomb", 1.7, args.study_iters), ("landau", args.config3_omega, args.study_iters)):
+        h = gf.gf_create(dims, gauge, "mixed")
+        if os.path.isdir(logdir):
+            gf.gf_set_check_log(h, os.path.join(logdir, f"config3_{gauge}_checks.jsonl"))
+        gf.gf_load_links_device(h, 0, src.data_ptr())
+        gf.gf_random_gauge_transform(h, 2)
+        r = gf.gf_fix(h, "or", omega, 1e-12, max_sweeps=cap, check_interval=20, reunit_interval=100,
+                      switch_theta=1e-8, raise_on_notconv=False)
+        Ft, Tt = gf.gf_slice_functional_theta(h)
+        F, T = gf.gf_functional_theta(h)
+        gf.gf_destroy(h)
+        out[gauge] = {"omega": omega, "seconds": r["seconds"], "sweeps": r["sweeps"],
+                      "sweeps_fp32": r["sweeps_fp32"], "sweeps_fp64": r["sweeps_fp64"],
+                      "converged": r["converged"], "site_updates_per_s": r["site_updates"] / r["seconds"],
+                      "F": float(F[0]), "theta": float(T[0]), "theta_slice_max": float(Tt[0].max()),
+                      "slices_below_1e-12": int((Tt[0] < 1e-12).sum())}
+        log("config3", gauge, json.dumps(out[gauge]))
+    print(json.dumps({"study": "config3", **out}), flush=True)
+
+
+def run_config4_study(args):
+    """Sec. 6.5's protocol on 16 Gribov copies per lattice (MAG, 24^4 and
+    32^4, eps = 0.3 field seed 3, copy k on the orbit point of Haar seed
+    3000 + k, all copies in one batched context): simulated annealing T 1.45 ->
+    0.01 over 3000 steps (heat bath + three microcanonical sweeps each), at
+    most 2000 stochastic-relaxation sweeps (p = 0.5, a copy leaves at theta <
+    1e-6), then overrelaxation omega = 1.35 to theta < 1e-12 in GF_MIXED
+    (FP64 below 1e-8); the best functional is kept."""
+    from paper_1212_5221_gb300 import build, gf, inputs
+
+    build.build_all()
+    out = {}
+    for dims in ((24, 24, 24, 24), (32, 32, 32, 32)):
+        U = inputs.links(dims, "smooth", 0.3, 3)
+        n = 16
+        h = gf.gf_create_batch(dims, n, "mag", "mixed")
+        gf.gf_load_links(h, -1, U)
+        gf.gf_set_copy_base(h, 3000)
+        gf.gf_random_gauge_transform(h, 3000)
+        r = gf.gf_protocol(h, args.config4_sa_steps, 1.45, 0.01, sr_sweeps=2000, sr_p=0.5, sr_theta=1e-6,
+                           seed=4, omega=1.35, theta_target=1e-12, max_sweeps=args.study_iters,
+                           check_interval=20, reunit_interval=100, switch_theta=1e-8, raise_on_notconv=False)
+        F, T = gf.gf_functional_theta(h)
+        gf.gf_destroy(h)
+        key = "x".join(map(str, dims))
+        out[key] = {"copies": n, "seconds": r["seconds"], "sweeps": r["sweeps"], "sweeps_fp32": r["sweeps_fp32"],
+                    "sweeps_fp64": r["sweeps_fp64"], "converged": r["converged"],
+                    "copies_below_1e-12": int((T < 1e-12).sum()), "theta_max": float(T.max()),
+                    "F_best": float(F.max()), "F_copies": [float(x) for x in F],
+                    "site_updates_per_s": r["site_updates"] / r["seconds"]}
+        log("config4", key, json.dumps(out[key]))
+    print(json.dumps({"study": "config4", "gauge": "mag", "sa_steps": args.config4_sa_steps, **out}), flush=True)
+
+
 def run_kernel_target(args):
     """Short, fixed launch sequences on the workload's lattice for ncu captures.
     fp32 / fp64 / mixed: 3 sweeps in that precision (mixed: FP32 sweeps that
@@ -742,8 +836,11 @@ def main():
     ap.add_argument("--max-sweeps", type=int, default=40000)
     ap.add_argument("--deep-switch", type=float, default=1e-13,
                     help="also time one mixed run with the FP32 -> FP64 switch at this theta (0: skip)")
-    ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="end-to-end steps through host buffers, on the orbit seeds of the first timed steps")
+    ap.add_argument("--fp64-matched", type=int, default=3,
+                    help="plain-FP64 runs on the orbit seeds of the first timed steps (time-to-theta ratio)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-fp64-baseline", dest="fp64_baseline", action="store_false")
     ap.add_argument("--kernel-target", choices=["fp32", "fp64", "mixed", "window"], default=None,
                     help="only run a short, fixed launch sequence of the workload (for ncu)")
@@ -754,10 +851,13 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-loads", type=lambda v: [float(x) for x in v.split(",") if x], default=[0.7],
                     help="Poisson rates as fractions of the measured saturated job rate")
-    ap.add_argument("--study", choices=["precision", "sa-temperature", "fullsize"], default=None,
+    ap.add_argument("--study", choices=["precision", "sa-temperature", "fullsize", "config3", "config4"], default=None,
                     help="run a report study instead of the benchmark")
     ap.add_argument("--study-iters", type=int, default=None)
     ap.add_argument("--study-every", type=int, default=2000)
+    ap.add_argument("--config3-omega", type=float, default=1.7,
+                    help="overrelaxation parameter of the 64^3x256 Landau fix (Coulomb uses 1.7)")
+    ap.add_argument("--config4-sa-steps", type=int, default=3000)
     args = ap.parse_args()
     if args.study == "precision":
         args.study_iters = args.study_iters or 12000
@@ -766,6 +866,14 @@ def main():
     if args.study == "fullsize":
         args.study_iters = args.study_iters or 8000
         run_fullsize_study(args)
+        return
+    if args.study == "config3":
+        args.study_iters = args.study_iters or 30000
+        run_config3_study(args)
+        return
+    if args.study == "config4":
+        args.study_iters = args.study_iters or 40000
+        run_config4_study(args)
         return
     if args.study == "sa-temperature":
         args.study_iters = args.study_iters or 10000

@@ -363,6 +363,8 @@ typedef struct {
   int converged;         /* 1 if every unit reached theta_target */
   double seconds;        /* host wall time of the call */
   uint64_t site_updates; /* sum over sweeps of the sites actually updated */
+  double F_mean;         /* at the last theta evaluation: the functional averaged over the copies */
+  double theta_max;      /* ... and the largest theta of any unit (copy, or Coulomb time-slice) */
 } gf_fix_result;
 
 int gf_fix(gf_ctx* ctx, const gf_fix_params* params, gf_fix_result* result);
@@ -450,8 +452,9 @@ int gf_functional_theta_noalloc(const int dims[4], gf_gauge gauge, const double*
  * go to the next job.  A job: load host_links (natural order; the caller keeps
  * the array alive until the job's result is polled), apply
  * gf_random_gauge_transform(orbit_seed) unless orbit_seed is 0, run gf_fix
- * with `fix`, then report F/theta and, if host_out is given, store the links
- * there.  Times are seconds since the server was created. */
+ * with `fix` (or gf_protocol with `protocol` when `anneal` is set), then
+ * report F/theta and, if host_out is given, store the links there.  Times
+ * are seconds since the server was created. */
 typedef struct gf_server gf_server;
 
 typedef struct {
@@ -463,6 +466,10 @@ typedef struct {
   gf_fix_params fix;
   double* host_out;
   uint64_t tag;          /* returned with the result */
+  int anneal;            /* 1: run gf_protocol with `protocol` instead of gf_fix with `fix` (simulated
+                            annealing and stochastic relaxation before the overrelaxation, Sec. 6.5:
+                            for MAG, whose overrelaxation alone converges slowly from a random gauge) */
+  gf_protocol_params protocol;
 } gf_job;
 
 typedef struct {

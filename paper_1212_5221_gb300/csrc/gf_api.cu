@@ -1339,6 +1339,14 @@ int gf_fix(gf_ctx* c, const gf_fix_params* P, gf_fix_result* res) {
         unit_theta[k] = s / Nt;
       }
     }
+    {  // what the result reports about the last evaluation
+      double fs = 0, tm = 0;
+      for (int k = 0; k < c->ncopies; ++k)
+        for (int t = 0; t < Nt; ++t) fs += ct[2 * ((size_t)k * Nt + t)];
+      for (double th : unit_theta) tm = std::max(tm, th);
+      R.F_mean = fs / ((double)c->ncopies * Nt);
+      R.theta_max = tm;
+    }
     const bool final_phase = c->fp64 || c->prec == GF_FP32 || c->prec == GF_MP;
     for (int k = 0; k < c->ncopies; ++k)
       for (int u = 0; u < units_per_copy; ++u) {
@@ -1538,6 +1546,8 @@ int gf_protocol(gf_ctx* c, const gf_protocol_params* P, gf_fix_result* res) {
   R.checks += F.checks;
   R.site_updates += F.site_updates;
   R.converged = F.converged;
+  R.F_mean = F.F_mean;
+  R.theta_max = F.theta_max;
   R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   if (res) *res = R;
   return r;

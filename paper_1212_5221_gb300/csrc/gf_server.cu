@@ -124,7 +124,7 @@ void run_job(const gf_job& J, char* mem, size_t bytes, gf_job_result& R) {
   if (!r && J.orbit_seed) r = gf_random_gauge_transform(c, J.orbit_seed);
   gf_fix_result fr;
   memset(&fr, 0, sizeof fr);
-  if (!r) r = gf_fix(c, &J.fix, &fr);
+  if (!r) r = J.anneal ? gf_protocol(c, &J.protocol, &fr) : gf_fix(c, &J.fix, &fr);
   const int fix_status = r;
   if (c && (r == GF_OK || r == GF_ENOTCONV)) {
     int r2 = gf_functional_theta(c, &R.F, &R.theta);

@@ -161,7 +161,13 @@ __device__ __forceinline__ void prefetch_tile(const SweepArgs<R>& a, uint32_t co
                                               int job) {
   constexpr int NC = store_traits<R>::NC;
   const int chunk = job % NC;
-  const int k = job / NC;  // slot 0..7: mu = k >> 1, down = k & 1
+  const int k = job / NC;  // slot 0..7: mu = k >> 1, down = k & 1; 8: the accumulator
+  if (k == 8) {  // GF_MIXED's accumulated transformation of the tile's sites (slot 4)
+    if (GAUGE == COULOMB || !a.acc) return;
+    const auto* base = a.links + link_off(copy, a.parity, 4, a.NS, NC, a.geom.Vh, 0) + (size_t)chunk * a.geom.Vh;
+    prefetch_l2(base + sp0, n * 16u);
+    return;
+  }
   const int mu = k >> 1;
   const bool down = k & 1;
   if (GAUGE == COULOMB && mu == 0 && down) return;  // idle slot
@@ -372,7 +378,7 @@ __device__ __forceinline__ void sweep_site_mag(const SweepArgs<R>& a, uint32_t c
   // periodically by the driver instead.  A read-only pass leaves them as stored.
   const bool NORM = (sizeof(R) == 4 || ALGO != ALG_OR) && (!OBS || a.update);
   mat3<R> u[LPT];
-  size_t off[LPT];
+  uint32_t idx[LPT];  // parity index of each slot's link (its offset is recomputed at the store)
   bool use[LPT];
 #pragma unroll
   for (int j = 0; j < LPT; ++j) {
@@ -390,9 +396,9 @@ __device__ __forceinline__ void sweep_site_mag(const SweepArgs<R>& a, uint32_t c
       ssp = (cm > 0 ? s - st : s + (uint32_t)(nm - 1) * st) >> 1;
       par ^= 1;
     }
-    off[j] = link_off(copy, par, mu, a.NS, NC, Vh, ssp);
+    idx[j] = ssp;
     if (use[j]) {
-      load_slot<R, TILE>(stage, G, sp0, k, ssp, a.links + off[j], Vh, u[j]);
+      load_slot<R, TILE>(stage, G, sp0, k, ssp, a.links + link_off(copy, par, mu, a.NS, NC, Vh, ssp), Vh, u[j]);
       if (NORM) reproject_rows(u[j]);
       reconstruct_row2(u[j]);
       if (down) dagger(u[j]);
@@ -479,9 +485,10 @@ __device__ __forceinline__ void sweep_site_mag(const SweepArgs<R>& a, uint32_t c
 #pragma unroll
   for (int j = 0; j < LPT; ++j) {
     if (!use[j]) continue;
-    const bool down = (LPT >= 2) ? (j & 1) : ((lane * LPT + j) & 1);
+    const int k = lane * LPT + j;
+    const bool down = (LPT >= 2) ? (j & 1) : (k & 1);
     if (down) dagger(u[j]);
-    store_rows(a.links + off[j], Vh, u[j]);
+    store_rows(a.links + link_off(copy, a.parity ^ (int)down, k >> 1, a.NS, NC, Vh, idx[j]), Vh, u[j]);
   }
 }
 
@@ -524,57 +531,65 @@ __device__ __forceinline__ quat<R> choose_k(cx<R> W00, cx<R> W01, cx<R> W10, cx<
   return g;
 }
 
-// FP64 contribution of a slot to K, from its stored rows (row 2 rebuilt in
-// FP64: what a later read of the links gives).
+// What F and theta need of K = sum of the site's slot matrices M, in FP64:
+// the antihermitian part of K, as ah[0..2] = Im K_aa, ah[3..5] = Re(K_ab -
+// K_ba) and ah[6..8] = Im(K_ab + K_ba) for (a,b) = (0,1), (0,2), (1,2), and
+// ah[9] = Re tr K (10 reals instead of K's 18).  A down slot M = D^dag
+// contributes minus the antihermitian part of D and Re tr D.  Each slot is
+// taken from its stored rows, row 2 rebuilt in FP64 (what a later read gives).
 template <typename R>
-__device__ __forceinline__ void add_stored_fp64(const mat3<R>& rows, bool down, double (&kr)[3][3],
-                                                double (&ki)[3][3]) {
+__device__ __forceinline__ void add_stored_ah(const mat3<R>& rows, bool down, double (&ah)[10]) {
   mat3<double> d;
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) d.e[a][b] = {(double)rows.e[a][b].re, (double)rows.e[a][b].im};
   reconstruct_row2(d);
+  const double sg = down ? -1.0 : 1.0;
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < 3; ++a) ah[a] += sg * d.e[a][a].im;
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      kr[a][b] += down ? d.e[b][a].re : d.e[a][b].re;
-      ki[a][b] += down ? -d.e[b][a].im : d.e[a][b].im;
-    }
+  for (int p = 0; p < 3; ++p) {
+    const int a = p == 2 ? 1 : 0, b = p == 0 ? 1 : 2;
+    ah[3 + p] += sg * (d.e[a][b].re - d.e[b][a].re);
+    ah[6 + p] += sg * (d.e[a][b].im + d.e[b][a].im);
+  }
+  ah[9] += d.e[0][0].re + d.e[1][1].re + d.e[2][2].re;
 }
 
-// theta_site = tr[Delta Delta^dag], Delta = traceless part of (K - K^dag)/(2i).
-__device__ __forceinline__ double theta_of_k(const double (&kr)[3][3], const double (&ki)[3][3]) {
-  double dr[3][3], di[3][3], th = 0.0;
+// The same ten reals of a gathered K.
+template <typename R>
+__device__ __forceinline__ void ah_of_k(const mat3<R>& K, double (&ah)[10]) {
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < 3; ++a) ah[a] = (double)K.e[a][a].im;
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      dr[a][b] = 0.5 * (ki[a][b] + ki[b][a]);
-      di[a][b] = -0.5 * (kr[a][b] - kr[b][a]);
-    }
-  const double tr3 = (dr[0][0] + dr[1][1] + dr[2][2]) / 3.0;
+  for (int p = 0; p < 3; ++p) {
+    const int a = p == 2 ? 1 : 0, b = p == 0 ? 1 : 2;
+    ah[3 + p] = (double)K.e[a][b].re - (double)K.e[b][a].re;
+    ah[6 + p] = (double)K.e[a][b].im + (double)K.e[b][a].im;
+  }
+  ah[9] = (double)K.e[0][0].re + (double)K.e[1][1].re + (double)K.e[2][2].re;
+}
+
+// theta_site = tr[Delta Delta^dag], Delta = traceless part of (K - K^dag)/(2i):
+// its diagonal is Im K_aa minus their mean, its (a,b) and (b,a) entries have
+// real part (Im K_ab + Im K_ba)/2 and imaginary parts -/+ (Re K_ab - Re K_ba)/2.
+__device__ __forceinline__ double theta_of_ah(const double (&ah)[10]) {
+  const double tr3 = (ah[0] + ah[1] + ah[2]) / 3.0;
+  double th = 0.0;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) dr[a][a] -= tr3;
+  for (int a = 0; a < 3; ++a) th += (ah[a] - tr3) * (ah[a] - tr3);
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) th += dr[a][b] * dr[a][b] + di[a][b] * di[a][b];
+  for (int p = 0; p < 3; ++p) th += 0.5 * (ah[3 + p] * ah[3 + p] + ah[6 + p] * ah[6 + p]);
   return th;
 }
 
 template <int L>
-__device__ __forceinline__ void butterfly_k(double (&kr)[3][3], double (&ki)[3][3]) {
+__device__ __forceinline__ void butterfly_ah(double (&ah)[10]) {
 #pragma unroll
   for (int o = 1; o < L; o <<= 1)
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        kr[a][b] += __shfl_xor_sync(FULL, kr[a][b], o);
-        ki[a][b] += __shfl_xor_sync(FULL, ki[a][b], o);
-      }
+    for (int k = 0; k < 10; ++k) ah[k] += __shfl_xor_sync(FULL, ah[k], o);
 }
 
 // rows 0,1 of G t (t with all three rows)
@@ -633,6 +648,10 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
   // for FP64 with eight links per lane and the fused-observables variants,
   // which read them again (from L2) instead of spilling
   constexpr bool KEEP = sizeof(R) == 4 ? !OBS : LPT <= 4;
+  // FP64 links read again for the update keep the rebuilt third rows of the
+  // up-links from the gather in shared memory (48 KB per block): Step 2 then
+  // rebuilds none of them (the same values, 96 FP64 operations less per site)
+  constexpr bool ROW2C = sizeof(R) == 8 && !KEEP && !MP && LPT == 8;
   const Geom& Gm = a.geom;
   const uint32_t Vh = Gm.Vh;
   int c[4] = {0, 0, 0, 0};
@@ -672,19 +691,19 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
   }
 
   // gather: K = sum of U_mu(x) and U_mu(x - mu)^dag over the lane's slots
+  __shared__ cx<R> row2c[ROW2C ? 12 * BLOCK : 1];
+  cx<R>* const r2c = row2c + (ROW2C ? threadIdx.x : 0);  // this thread's column: [up-link][entry] stride BLOCK
   mat3<R> u[KEEP ? LPT : 1];
   mat3<S> K;
 #pragma unroll
   for (int x = 0; x < 3; ++x)
 #pragma unroll
     for (int y = 0; y < 3; ++y) K.e[x][y] = {S(0), S(0)};
-  constexpr bool OBS_FP64 = OBS && sizeof(R) == 4;  // FP32 kernels gather the FP64 K separately
-  double kr[3][3], ki[3][3];
+  constexpr bool OBS_FP64 = OBS && sizeof(R) == 4;  // FP32 kernels gather the FP64 sums separately
+  double ah[10];
   if (OBS) {
 #pragma unroll
-    for (int x = 0; x < 3; ++x)
-#pragma unroll
-      for (int y = 0; y < 3; ++y) kr[x][y] = ki[x][y] = 0.0;
+    for (int k = 0; k < 10; ++k) ah[k] = 0.0;
   }
 #pragma unroll
   for (int j = 0; j < LPT; ++j) {
@@ -697,11 +716,17 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
     }
     if (KEEP) u[KEEP ? j : 0] = t;
     if (use[j] && gather[j]) {
-      if (OBS_FP64 && a.obs == 1) add_stored_fp64(t, dn[j], kr, ki);
+      if (OBS_FP64 && a.obs == 1) add_stored_ah(t, dn[j], ah);
       if constexpr (MP) {
         add_stored_k64(t, dn[j], K);
       } else {
         reconstruct_row2(t);
+        if constexpr (ROW2C) {
+          if (!dn[j]) {
+#pragma unroll
+            for (int y = 0; y < 3; ++y) r2c[((j >> 1) * 3 + y) * BLOCK] = t.e[2][y];
+          }
+        }
 #pragma unroll
         for (int x = 0; x < 3; ++x)
 #pragma unroll
@@ -724,18 +749,11 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
       }
 
   if (OBS && a.obs == 1) {  // theta of the current links at this site (K as gathered)
-    if (OBS_FP64) {
-      butterfly_k<L>(kr, ki);
-    } else {
-#pragma unroll
-      for (int x = 0; x < 3; ++x)
-#pragma unroll
-        for (int y = 0; y < 3; ++y) {
-          kr[x][y] = (double)K.e[x][y].re;
-          ki[x][y] = (double)K.e[x][y].im;
-        }
-    }
-    if (valid && lane == 0) a.obs_site[(size_t)copy * Gm.V + s] = make_double2(0.0, theta_of_k(kr, ki));
+    if (OBS_FP64)
+      butterfly_ah<L>(ah);
+    else
+      ah_of_k(K, ah);
+    if (valid && lane == 0) a.obs_site[(size_t)copy * Gm.V + s] = make_double2(0.0, theta_of_ah(ah));
   }
   if (OBS && !a.update) return;
 
@@ -797,12 +815,9 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
   }
 
   // Step 2: apply G to the slots; fused F and theta of the written links
-  double F = 0.0;
   if (OBS && a.obs == 2) {
 #pragma unroll
-    for (int x = 0; x < 3; ++x)
-#pragma unroll
-      for (int y = 0; y < 3; ++y) kr[x][y] = ki[x][y] = 0.0;
+    for (int k = 0; k < 10; ++k) ah[k] = 0.0;
   }
 #pragma unroll
   for (int j = 0; j < LPT; ++j) {
@@ -817,16 +832,20 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
     if (dn[j]) {
       apply_right_dag(G, t, n);
     } else {
-      reconstruct_row2(t);
+      if (ROW2C && gather[j]) {
+#pragma unroll
+        for (int y = 0; y < 3; ++y) t.e[2][y] = r2c[((j >> 1) * 3 + y) * BLOCK];
+      } else {
+        reconstruct_row2(t);
+      }
       apply_left(G, t, n);
     }
     store_rows(a.links + off[j], Vh, n);
-    if (OBS && a.obs == 2 && gather[j]) add_stored_fp64(n, dn[j], kr, ki);
+    if (OBS && a.obs == 2 && gather[j]) add_stored_ah(n, dn[j], ah);
   }
   if (OBS && a.obs == 2) {
-    butterfly_k<L>(kr, ki);
-    F = kr[0][0] + kr[1][1] + kr[2][2];
-    if (valid && lane == 0) a.obs_site[(size_t)copy * Gm.V + s] = make_double2(F, theta_of_k(kr, ki));
+    butterfly_ah<L>(ah);
+    if (valid && lane == 0) a.obs_site[(size_t)copy * Gm.V + s] = make_double2(ah[9], theta_of_ah(ah));
   }
 }
 
@@ -834,14 +853,15 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
 // 256 threads; 1 / 2 / 3 / 4 blocks allow 255 / 128 / 80 / 64 registers):
 // FP32 1 / 2 / 3 / 4 blocks for 8 / 4 / 2 / 1 links per lane.  FP64 in K form
 // 2 / 1 / 1 / 2 (eight links per lane read the links again for the update);
-// the per-slot MAG form 1 / 1 / 2 / 3.  (Reading the links again in FP32 as
-// well, to fit one more block, measured slower: 0.347 against 0.324 ms per
-// 32^3 x 64 sweep.)
+// the per-slot MAG form 1 / 1 / 1 / 2 (FP64 MAG runs eight links per lane as
+// four: eight full FP64 matrices per lane do not fit in registers).  (Reading
+// the links again in FP32 as well, to fit one more block, measured slower:
+// 0.347 against 0.324 ms per 32^3 x 64 sweep.)
 template <typename R, int GAUGE, int LPT, bool MP = false>
 constexpr int min_blocks() {
   if (MP) return LPT == 8 ? 1 : LPT == 4 ? 1 : LPT == 2 ? 2 : 3;  // FP64 K and G in registers
   if (sizeof(R) == 4) return LPT == 8 ? 1 : LPT == 4 ? 2 : LPT == 2 ? 3 : 4;
-  return GAUGE == MAG ? (LPT >= 4 ? 1 : LPT == 2 ? 2 : 3) : (LPT == 8 ? 2 : LPT >= 2 ? 1 : 2);
+  return GAUGE == MAG ? (LPT >= 2 ? 1 : 2) : (LPT == 8 ? 2 : LPT >= 2 ? 1 : 2);
 }
 
 template <typename R, int GAUGE, int ALGO, int LPT, bool OBS, bool MP>
@@ -941,7 +961,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R, GAUGE, LPT, MP>()) sweep_
   const uint32_t local = threadIdx.x / L;
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const uint64_t next = tile + gridDim.x;
-    if (a.prefetch && next < ntiles && threadIdx.x < 8 * NC) {
+    if (a.prefetch && next < ntiles && threadIdx.x < 9 * NC) {
       const uint32_t nc = (uint32_t)(next / tiles_per_copy);
       const uint32_t nsp0 = (uint32_t)(next - (uint64_t)nc * tiles_per_copy) * TILE;
       prefetch_tile<R, GAUGE>(a, nc, nsp0, min(TILE, Vh - nsp0), (int)threadIdx.x);

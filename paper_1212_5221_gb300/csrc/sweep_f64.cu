@@ -43,7 +43,11 @@ static cudaError_t launch_lpt(const SweepArgs<R>& a, int lpt, cudaStream_t st) {
     case 1: return launch_one<R, GAUGE, ALGO, 1>(a, st);
     case 2: return launch_one<R, GAUGE, ALGO, 2>(a, st);
     case 4: return launch_one<R, GAUGE, ALGO, 4>(a, st);
-    case 8: return launch_one<R, GAUGE, ALGO, 8>(a, st);
+    case 8:
+      // the MAG per-slot form holds every slot as a full 3x3 matrix: eight
+      // FP64 matrices per lane would spill, so eight links per lane run as four
+      if constexpr (GAUGE == MAG) return launch_one<R, GAUGE, ALGO, 4>(a, st);
+      else return launch_one<R, GAUGE, ALGO, 8>(a, st);
   }
   return cudaErrorInvalidValue;
 }

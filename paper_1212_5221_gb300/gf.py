@@ -53,7 +53,8 @@ class gf_protocol_params(ctypes.Structure):
 class gf_job(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int * 4), ("gauge", ctypes.c_int), ("prec", ctypes.c_int),
                 ("host_links", ctypes.c_void_p), ("orbit_seed", ctypes.c_uint64), ("fix", gf_fix_params),
-                ("host_out", ctypes.c_void_p), ("tag", ctypes.c_uint64)]
+                ("host_out", ctypes.c_void_p), ("tag", ctypes.c_uint64), ("anneal", ctypes.c_int),
+                ("protocol", gf_protocol_params)]
 
 
 class gf_job_result(ctypes.Structure):
@@ -70,7 +71,7 @@ class gf_job_result(ctypes.Structure):
 class gf_fix_result(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("sweeps_fp32", ctypes.c_int), ("sweeps_fp64", ctypes.c_int),
                 ("checks", ctypes.c_int), ("converged", ctypes.c_int), ("seconds", ctypes.c_double),
-                ("site_updates", ctypes.c_uint64)]
+                ("site_updates", ctypes.c_uint64), ("F_mean", ctypes.c_double), ("theta_max", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -513,9 +514,11 @@ def gf_server_create_mock(hbm_bytes, slots, seconds_per_gb):
 
 def gf_server_submit(s, dims, gauge="landau", prec="mixed", host_links=None, orbit_seed=0, tag=0,
                      host_out=None, algo="or", param=1.7, theta_target=1e-12, max_sweeps=100000,
-                     check_interval=20, reunit_interval=100, switch_theta=1e-8):
+                     check_interval=20, reunit_interval=100, switch_theta=1e-8, anneal=None):
     """Queue a job; host_links / host_out (numpy complex128, natural order) must stay
-    alive until the job's result has been polled."""
+    alive until the job's result has been polled.  anneal: None (gf_fix), or a dict
+    with sa_steps, T_start, T_end, sr_sweeps, sr_p, sr_theta, seed for gf_protocol
+    (whose overrelaxation stage takes the other fix arguments)."""
     j = gf_job()
     j.dims[:] = [int(d) for d in dims]
     j.gauge = _enum(gauge, GAUGES)
@@ -526,6 +529,12 @@ def gf_server_submit(s, dims, gauge="landau", prec="mixed", host_links=None, orb
                           int(check_interval), int(reunit_interval), float(switch_theta), 0)
     j.host_out = None if host_out is None else _links_arg(host_out)
     j.tag = int(tag)
+    if anneal:
+        a = dict(sa_steps=0, T_start=1.45, T_end=0.01, sr_sweeps=0, sr_p=0.5, sr_theta=0.0, seed=0, **anneal)
+        j.anneal = 1
+        j.protocol = gf_protocol_params(int(a["sa_steps"]), float(a["T_start"]), float(a["T_end"]),
+                                        int(a["sr_sweeps"]), float(a["sr_p"]), float(a["sr_theta"]),
+                                        int(a["seed"]), j.fix)
     _check(lib().gf_server_submit(s, ctypes.byref(j)), "gf_server_submit")
 
 

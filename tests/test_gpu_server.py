@@ -59,3 +59,41 @@ def test_server_results_equal_alone(gf, synth):
         assert r["sweeps"] == r1["sweeps"]
         assert r["F"] == F[0] and r["theta"] == T[0]
         assert np.array_equal(V, outs[k])
+
+
+def test_server_protocol_job_equals_alone(gf, synth):
+    """A MAG job run through the annealing protocol (SA -> SR -> OR, Sec. 6.5)
+    in the server, beside plain jobs, gives the links the same protocol gives
+    on its own context."""
+    dims = (6, 6, 6, 6)
+    u = synth.links(dims, "smooth", 0.3, 7)
+    other = synth.links((8, 8, 8, 8), "smooth", 0.3, 8)
+    out = np.empty_like(u)
+    fix = dict(param=1.35, theta_target=1e-11, max_sweeps=20000, check_interval=10, switch_theta=1e-8)
+    ann = dict(sa_steps=50, T_start=1.45, T_end=0.01, sr_sweeps=200, sr_p=0.5, sr_theta=1e-6, seed=5)
+    s = gf.gf_server_create(gf.gf_footprint(dims, 1, "mag", "mixed") * 3 + (1 << 20), 2)
+    try:
+        gf.gf_server_submit(s, (8, 8, 8, 8), "landau", "mixed", host_links=other, orbit_seed=3, tag=1,
+                            param=1.7, theta_target=1e-11, max_sweeps=20000)
+        gf.gf_server_submit(s, dims, "mag", "mixed", host_links=u, orbit_seed=41, tag=2, host_out=out,
+                            anneal=ann, **fix)
+        res = []
+        t0 = time.time()
+        while len(res) < 2 and time.time() - t0 < 300:
+            res += gf.gf_server_poll(s, 8, 50)
+    finally:
+        gf.gf_server_destroy(s)
+    r = {x["tag"]: x for x in res}[2]
+    assert r["status"] == 0 and r["theta"] < 1e-11
+    h = gf.gf_create(dims, "mag", "mixed")
+    try:
+        gf.gf_load_links(h, 0, u)
+        gf.gf_random_gauge_transform(h, 41)
+        r1 = gf.gf_protocol(h, 50, 1.45, 0.01, sr_sweeps=200, sr_p=0.5, sr_theta=1e-6, seed=5, omega=1.35,
+                            theta_target=1e-11, max_sweeps=20000, check_interval=10, switch_theta=1e-8)
+        V = np.empty_like(u)
+        gf.gf_store_links(h, 0, V)
+    finally:
+        gf.gf_destroy(h)
+    assert r["sweeps"] == r1["sweeps"]
+    assert np.array_equal(V, out)
