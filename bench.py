@@ -470,7 +470,13 @@ def run_serving(args):
     the lattice's eps = 0.3 field, moved to a fresh point of its gauge orbit
     by the job's own Haar seed, to theta < --serve-theta (FP32 -> FP64 switch
     a decade below), at most --serve-max-sweeps sweeps; a job that reaches
-    the cap counts as finished and unconverged."""
+    the cap counts as finished and unconverged.  MAG jobs run the annealing
+    protocol of Sec. 6.5 first (--serve-mag-sa simulated-annealing steps T
+    1.45 -> 0.01, then stochastic relaxation until theta < 1e-6, at most
+    --serve-mag-sr sweeps), since their overrelaxation alone converges slowly
+    from a random gauge.  The saturated rate is measured on the first
+    --serve-sat-jobs jobs (all submitted at once); the Poisson stream of all
+    --serve-jobs jobs then arrives at each --serve-loads fraction of it."""
     import torch
 
     from paper_1212_5221_gb300 import build, gf, inputs
@@ -488,11 +494,11 @@ def run_serving(args):
     arena = int(min(0.6 * free, args.serve_slots * max(foot.values()) * 1.1))
     log(f"serving: {n} jobs, {args.serve_slots} slots, arena {arena / 1e9:.1f} GB")
 
-    def run(rate):
+    def run(rate, n_jobs):
         srv = gf.gf_server_create(arena, args.serve_slots)
         results, t0 = [], time.time()
         try:
-            for k, j in enumerate(jobs):
+            for k, j in enumerate(jobs[:n_jobs]):
                 if rate:
                     wait = j["arrival"] / rate - (time.time() - t0)
                     if wait > 0:
@@ -500,11 +506,15 @@ def run_serving(args):
                         while time.time() - t0 < j["arrival"] / rate:
                             results += gf.gf_server_poll(srv, 256, 1)
                 th = args.serve_theta
+                ann = None
+                if j["gauge"] == "mag" and (args.serve_mag_sa or args.serve_mag_sr):
+                    ann = dict(sa_steps=args.serve_mag_sa, T_start=1.45, T_end=0.01, sr_sweeps=args.serve_mag_sr,
+                               sr_p=0.5, sr_theta=1e-6, seed=j["seed"])
                 gf.gf_server_submit(srv, j["dims"], j["gauge"], "mixed", host_links=fields[j["dims"]],
                                     orbit_seed=j["seed"], tag=k, param=S["omega"][j["gauge"]], theta_target=th,
                                     max_sweeps=args.serve_max_sweeps, check_interval=S["check"],
-                                    reunit_interval=S["reunit"], switch_theta=th / 10)
-            while len(results) < n:
+                                    reunit_interval=S["reunit"], switch_theta=th / 10, anneal=ann)
+            while len(results) < n_jobs:
                 results += gf.gf_server_poll(srv, 256, 1000)
         finally:
             gf.gf_server_destroy(srv)
@@ -515,7 +525,13 @@ def run_serving(args):
         span = max(r["t_done"] for r in results) - t_first
         lat = np.array([r["t_done"] - r["t_submit"] for r in results])
         su = float(sum(r["site_updates"] for r in results))
-        return dict(jobs=n, seconds=span, jobs_per_s=n / span, site_updates_per_s=su / span,
+        by_gauge = {}
+        for r in results:
+            g = jobs[r["tag"]]["gauge"]
+            by_gauge.setdefault(g, []).append(r["t_done"] - r["t_submit"])
+        return dict(jobs=n_jobs, seconds=span, jobs_per_s=n_jobs / span, site_updates_per_s=su / span,
+                    p50_s_by_gauge={g: float(np.percentile(v, 50)) for g, v in by_gauge.items()},
+                    p99_s_by_gauge={g: float(np.percentile(v, 99)) for g, v in by_gauge.items()},
                     p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
                     mean_s=float(lat.mean()), max_s=float(lat.max()),
                     queue_p50_s=float(np.percentile([r["t_admit"] - r["t_submit"] for r in results], 50)),
@@ -524,12 +540,12 @@ def run_serving(args):
                     sweeps=sum(r["sweeps"] for r in results))
 
     with Clocks(0) as clocks:
-        sat = run(0.0)
+        sat = run(0.0, min(args.serve_sat_jobs, n))
         log("saturated:", json.dumps(sat))
         loads = []
         for f in args.serve_loads:
             rate = f * sat["jobs_per_s"]
-            r = run(rate)
+            r = run(rate, n)
             r.update(load=f, rate_jobs_per_s=rate)
             loads.append(r)
             log("poisson:", json.dumps(r))
@@ -540,7 +556,10 @@ def run_serving(args):
             "config": {"workload": S["name"], "jobs": n, "stream_seed": S["seed"],
                        "lattices": ["16^4", "24^3x48", "32^4", "48^3x96"], "gauges": ["landau", "coulomb", "mag"],
                        "precision": "mixed", "theta_target": args.serve_theta,
-                       "max_sweeps": args.serve_max_sweeps, "slots": args.serve_slots, "arena_bytes": arena},
+                       "max_sweeps": args.serve_max_sweeps, "slots": args.serve_slots, "arena_bytes": arena,
+                       "mag_protocol": {"sa_steps": args.serve_mag_sa, "T": [1.45, 0.01],
+                                        "sr_sweeps_max": args.serve_mag_sr, "sr_theta": 1e-6},
+                       "saturated_prefix_jobs": min(args.serve_sat_jobs, n)},
             "p50_s": head["p50_s"], "p99_s": head["p99_s"], "site_updates_per_s": head["site_updates_per_s"],
             "saturated": sat, "poisson": loads, "clocks": clocks.summary()}
     print(json.dumps(line), flush=True)
@@ -847,8 +866,11 @@ def main():
     ap.add_argument("--serving", action="store_true", help="run the serving workload (job p50/p99)")
     ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--serve-theta", type=float, default=1e-10)
-    ap.add_argument("--serve-max-sweeps", type=int, default=5000)
+    ap.add_argument("--serve-max-sweeps", type=int, default=20000)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-sat-jobs", type=int, default=100, help="jobs of the saturated-rate run")
+    ap.add_argument("--serve-mag-sa", type=int, default=300, help="annealing steps of a MAG job")
+    ap.add_argument("--serve-mag-sr", type=int, default=1000, help="most stochastic-relaxation sweeps of a MAG job")
     ap.add_argument("--serve-loads", type=lambda v: [float(x) for x in v.split(",") if x], default=[0.7],
                     help="Poisson rates as fractions of the measured saturated job rate")
     ap.add_argument("--study", choices=["precision", "sa-temperature", "fullsize", "config3", "config4"], default=None,
