@@ -815,6 +815,48 @@ def run_config4_study(args):
     print(json.dumps({"study": "config4", "gauge": "mag", "sa_steps": args.config4_sa_steps, **out}), flush=True)
 
 
+def run_group_study(args):
+    """Small lattices of different extents (32 Landau lattices from 8^4 to
+    16^4, FP32 storage, eps = 0.4): overrelaxation sweeps of every lattice
+    on its own context and stream (the launches of all contexts overlap on
+    the device) against gf_group_sweep, one launch per half-sweep for all of
+    them; site-updates/s and launches per sweep of each."""
+    import torch
+
+    from paper_1212_5221_gb300 import build, gf, inputs
+
+    build.build_all()
+    specs = ([(8, 8, 8, 8)] * 8 + [(12, 12, 12, 12)] * 8 + [(16, 16, 16, 16)] * 8 + [(8, 8, 8, 16)] * 4 +
+             [(16, 12, 12, 12)] * 4)
+    n = args.study_iters
+    hs = [gf.gf_create(d, "landau", "fp32") for d in specs]
+    for k, (h, d) in enumerate(zip(hs, specs)):
+        gf.gf_load_links(h, 0, inputs.links(d, "smooth", 0.4, k))
+    sites = float(sum(np.prod(d) for d in specs))
+    out = {"lattices": len(specs), "sites": sites, "sweeps": n}
+    for mode in ("alone", "group"):
+        for rep in range(2):  # the first pass warms up (graphs, autotuned shapes)
+            n0 = sum(gf.gf_launch_count(h) for h in hs)
+            torch.cuda.synchronize()
+            t0 = time.time()
+            if mode == "alone":
+                for h in hs:
+                    gf.gf_sweep_async(h, "or", 1.7, n)
+                for h in hs:
+                    gf.gf_synchronize(h)
+            else:
+                gf.gf_group_sweep(hs, "or", 1.7, n)
+            torch.cuda.synchronize()
+            dt = time.time() - t0
+            launches = sum(gf.gf_launch_count(h) for h in hs) - n0
+        out[mode] = {"seconds": dt, "site_updates_per_s": n * sites / dt, "launches_per_sweep": launches / n}
+        log("group study", mode, json.dumps(out[mode]))
+    for h in hs:
+        gf.gf_destroy(h)
+    out["speedup_group_vs_alone"] = out["group"]["site_updates_per_s"] / out["alone"]["site_updates_per_s"]
+    print(json.dumps({"study": "group", **out}), flush=True)
+
+
 def run_kernel_target(args):
     """Short, fixed launch sequences on the workload's lattice for ncu captures.
     fp32 / fp64 / mixed: 3 sweeps in that precision (mixed: FP32 sweeps that
@@ -873,7 +915,8 @@ def main():
     ap.add_argument("--serve-mag-sr", type=int, default=1000, help="most stochastic-relaxation sweeps of a MAG job")
     ap.add_argument("--serve-loads", type=lambda v: [float(x) for x in v.split(",") if x], default=[0.7],
                     help="Poisson rates as fractions of the measured saturated job rate")
-    ap.add_argument("--study", choices=["precision", "sa-temperature", "fullsize", "config3", "config4"], default=None,
+    ap.add_argument("--study", choices=["precision", "sa-temperature", "fullsize", "config3", "config4", "group"],
+                    default=None,
                     help="run a report study instead of the benchmark")
     ap.add_argument("--study-iters", type=int, default=None)
     ap.add_argument("--study-every", type=int, default=2000)
@@ -888,6 +931,10 @@ def main():
     if args.study == "fullsize":
         args.study_iters = args.study_iters or 8000
         run_fullsize_study(args)
+        return
+    if args.study == "group":
+        args.study_iters = args.study_iters or 200
+        run_group_study(args)
         return
     if args.study == "config3":
         args.study_iters = args.study_iters or 30000

@@ -441,6 +441,31 @@ int gf_launch_count(gf_ctx* ctx, uint64_t* n);
 int gf_functional_theta_noalloc(const int dims[4], gf_gauge gauge, const double* device_links, void* stream,
                                 double* F, double* theta, double* F_t, double* theta_t);
 
+/* ---- Several lattices in one launch ---------------------------------------
+ * A group is 1..GF_GROUP_MAX contexts of any lattice extents and copy counts,
+ * one gauge, on one device (GF_FP32, GF_FP64 or GF_MIXED storage; not GF_MP,
+ * not time slabs).  Every half-sweep of all members is a single persistent
+ * launch over the union of their tiles (members in FP32 and in FP64 storage
+ * go in one launch each), issued on the first member's stream; the other
+ * members' streams are ordered before and after it with events.  Small
+ * lattices, whose own launches would leave most of the GPU idle, fill it
+ * together.  The paper has no counterpart (its batching is over time-slices
+ * of one lattice); each member's links come out exactly as if it had been
+ * swept alone with the same links-per-thread.
+ * gf_group_sweep: n_sweeps sweeps of GF_OR (omega = param) or GF_RELAX, then
+ * GF_MIXED members' FP64 masters are brought up to date; synchronous. */
+#define GF_GROUP_MAX 48
+int gf_group_sweep(gf_ctx* const* ctxs, int n, gf_algo algo, double param, int n_sweeps);
+
+/* gf_fix for every member of a group: theta is evaluated per member every
+ * check_interval sweeps (a fixed cadence, by the standalone FP64 pass),
+ * each unit (copy or Coulomb time-slice) stops on its own, a GF_MIXED member
+ * switches to its FP64 master on its own below switch_theta, and the members
+ * still sweeping share the launches; re-unitarisation as in gf_fix.
+ * results: n entries (may be NULL).  GF_ENOTCONV if any member did not
+ * reach theta_target within max_sweeps. */
+int gf_group_fix(gf_ctx* const* ctxs, int n, const gf_fix_params* params, gf_fix_result* results);
+
 /* Job server: many gauge-fixing jobs (different lattices, gauges and
  * precisions) share the GPU.  gf_server_create reserves hbm_bytes of device
  * memory once and starts `slots` worker threads.  A submitted job waits in a

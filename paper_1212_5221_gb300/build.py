@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgf.so")
-UNITS = ["sweep_f32.cu", "sweep_mp.cu", "sweep_f64.cu", "gf_aux.cu", "gf_api.cu", "gf_noalloc.cu", "gf_server.cu"]
+UNITS = ["sweep_f32.cu", "sweep_mp.cu", "sweep_f64.cu", "sweep_group.cu", "gf_aux.cu", "gf_api.cu", "gf_noalloc.cu", "gf_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -267,60 +267,46 @@ int default_lpt(const gf_ctx* c, int algo) {
   return c->fp64 ? 8 : 4;  // fastest on GB300 for the 32^3 x 64 Landau sweep
 }
 
+// The kernel arguments of one half-sweep of context c.
+template <typename R>
+void fill_args(gfk::SweepArgs<R>& a, gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, uint32_t sweep,
+               int obs, int update, int prefetch, const int* active_override) {
+  a.links = static_cast<typename gfk::store_traits<R>::vec*>(sizeof(R) == 8 ? c->links64 : c->links32);
+  a.geom = c->G;
+  a.NS = c->NS();
+  a.parity = parity;
+  a.ncopies = (uint32_t)c->ncopies;
+  a.copy0 = c->copy_base;
+  a.active = active_override ? active_override : (c->all_active ? nullptr : c->active_d);
+  a.param = (R)param;
+  a.k0 = (uint32_t)seed;
+  a.k1 = (uint32_t)(seed >> 32);
+  a.sweep = sweep;
+  a.prefetch = prefetch;
+  a.acc = (update && c->prec == GF_MIXED && !c->fp64 && c->gauge != GF_COULOMB) ? 1 : 0;
+  a.obs = obs;
+  a.update = update;
+  a.obs_site = static_cast<double2*>(c->obs_site);
+  a.err = c->err_d;
+  a.wait_polls = sizeof(R) == 8 ? -1 : c->stage_wait_polls;
+  a.sa_trace = kalgo == gfk::ALG_SA ? c->sa_trace_d : nullptr;
+  a.site_offset = c->site_offset;
+}
+
 int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, uint32_t sweep, int lpt,
                 int obs = 0, int update = 1, int pmode = -1, const int* active_override = nullptr) {
   const int prefetch = pmode >= 0 ? pmode : c->prefetch;
   cudaError_t e;
   if (c->fp64) {
     gfk::SweepArgs<double> a;
-    a.links = static_cast<double2*>(c->links64);
-    a.geom = c->G;
-    a.NS = c->NS();
-    a.parity = parity;
-    a.ncopies = (uint32_t)c->ncopies;
-    a.copy0 = c->copy_base;
-    a.active = c->all_active ? nullptr : c->active_d;
-    a.param = param;
-    a.k0 = (uint32_t)seed;
-    a.k1 = (uint32_t)(seed >> 32);
-    a.sweep = sweep;
-    a.prefetch = prefetch;
-    a.acc = (update && c->prec == GF_MIXED && !c->fp64 && c->gauge != GF_COULOMB) ? 1 : 0;
-    a.obs = obs;
-    a.update = update;
-    a.obs_site = static_cast<double2*>(c->obs_site);
-    a.err = c->err_d;
-    a.wait_polls = -1;
-    a.sa_trace = kalgo == gfk::ALG_SA ? c->sa_trace_d : nullptr;
-    a.site_offset = c->site_offset;
-    if (active_override) a.active = active_override;
+    fill_args(a, c, kalgo, param, parity, seed, sweep, obs, update, prefetch, active_override);
     cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<double>(a, c->gauge, kalgo, lpt, c->st);
     prof_end(c, t0, GF_KERNEL_SWEEP_FP64);
     c->launch_count++;
   } else {
     gfk::SweepArgs<float> a;
-    a.links = static_cast<float4*>(c->links32);
-    a.geom = c->G;
-    a.NS = c->NS();
-    a.parity = parity;
-    a.ncopies = (uint32_t)c->ncopies;
-    a.copy0 = c->copy_base;
-    a.active = c->all_active ? nullptr : c->active_d;
-    a.param = (float)param;
-    a.k0 = (uint32_t)seed;
-    a.k1 = (uint32_t)(seed >> 32);
-    a.sweep = sweep;
-    a.prefetch = prefetch;
-    a.acc = (update && c->prec == GF_MIXED && !c->fp64 && c->gauge != GF_COULOMB) ? 1 : 0;
-    a.obs = obs;
-    a.update = update;
-    a.obs_site = static_cast<double2*>(c->obs_site);
-    a.err = c->err_d;
-    a.wait_polls = c->stage_wait_polls;
-    a.sa_trace = kalgo == gfk::ALG_SA ? c->sa_trace_d : nullptr;
-    a.site_offset = c->site_offset;
-    if (active_override) a.active = active_override;
+    fill_args(a, c, kalgo, param, parity, seed, sweep, obs, update, prefetch, active_override);
     if (a.prefetch == GF_PREFETCH_SMEM) c->err_pending = true;
     cudaEvent_t t0 = prof_begin(c);
     e = c->prec == GF_MP ? gfk::launch_sweep_mp(a, c->gauge, kalgo, lpt, c->st)
@@ -761,6 +747,88 @@ int promote(gf_ctx* c) {
   return GF_OK;
 }
 
+// ---- Groups: several contexts (lattices of different extents) per launch ----
+
+static_assert(GF_GROUP_MAX == gfk::GROUP_MAX, "the group size limit of the ABI and of the kernel");
+
+int check_group(gf_ctx* const* ctxs, int n) {
+  if (!ctxs || n < 1 || n > gfk::GROUP_MAX) return fail(GF_EINVAL, "a group has 1..%d contexts", gfk::GROUP_MAX);
+  for (int k = 0; k < n; ++k) {
+    gf_ctx* c = ctxs[k];
+    if (!c) return fail(GF_EINVAL, "context %d of the group is NULL", k);
+    if (c->gauge != ctxs[0]->gauge) return fail(GF_EINVAL, "group members differ in gauge");
+    if (c->device != ctxs[0]->device) return fail(GF_EINVAL, "group members live on different devices");
+    if (c->prec == GF_MP) return fail(GF_EINVAL, "GF_MP contexts cannot be grouped");
+    if (c->slab) return fail(GF_EINVAL, "time slabs cannot be grouped");
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == c) return fail(GF_EINVAL, "context %d appears twice in the group", k);
+  }
+  return GF_OK;
+}
+
+// One half-sweep (overrelaxation, omega) of members that share their
+// storage precision, as one launch on the first member's stream; the other
+// members' streams are ordered before and after it with events.
+template <typename R>
+int group_half_t(const std::vector<gf_ctx*>& m, double omega, int parity) {
+  gf_ctx* c0 = m[0];
+  int lpt = default_lpt(c0, GF_OR);
+  if (c0->gauge == GF_MAG && sizeof(R) == 8 && lpt == 8) lpt = 4;  // as the single-lattice launcher
+  const uint32_t tile = gfk::BLOCK / (8 / lpt);
+  static thread_local gfk::GroupArgs<R> g;
+  uint64_t cum = 0;
+  for (size_t k = 0; k < m.size(); ++k) {
+    fill_args(g.m[k], m[k], gfk::ALG_OR, omega, parity, 0, (uint32_t)m[k]->sweep_index, 0, 1, GF_PREFETCH_NONE,
+              nullptr);
+    cum += (uint64_t)((m[k]->G.Vh + tile - 1) / tile) * (uint64_t)m[k]->ncopies;
+    g.tile_end[k] = cum;
+  }
+  g.n = (uint32_t)m.size();
+  g.ntiles = cum;
+  std::vector<cudaEvent_t> evs;
+  for (size_t k = 1; k < m.size(); ++k)
+    if (m[k]->st != c0->st) {
+      cudaEvent_t e = take_event(c0);
+      GF_CUDA(cudaEventRecord(e, m[k]->st));
+      GF_CUDA(cudaStreamWaitEvent(c0->st, e, 0));
+      evs.push_back(e);
+    }
+  cudaEvent_t t0 = prof_begin(c0);
+  cudaError_t e = gfk::launch_group<R>(g, c0->gauge, lpt, c0->st);
+  if (e != cudaSuccess) return fail(GF_ECUDA, "group sweep launch: %s", cudaGetErrorString(e));
+  prof_end(c0, t0, sizeof(R) == 8 ? GF_KERNEL_SWEEP_FP64 : GF_KERNEL_SWEEP_FP32);
+  c0->launch_count++;
+  if (!evs.empty()) {
+    cudaEvent_t done = take_event(c0);
+    GF_CUDA(cudaEventRecord(done, c0->st));
+    for (size_t k = 1; k < m.size(); ++k)
+      if (m[k]->st != c0->st) GF_CUDA(cudaStreamWaitEvent(m[k]->st, done, 0));
+    evs.push_back(done);
+  }
+  // a wait already enqueued refers to the event's record at the time of the
+  // call, so the events can be recorded again right away
+  for (cudaEvent_t ev : evs) c0->event_pool.push_back(ev);
+  return GF_OK;
+}
+
+// One full sweep of every member: members in FP32 storage and members in
+// FP64 storage (a GF_MIXED member after its switch) go in separate launches.
+int group_sweep_once(const std::vector<gf_ctx*>& members, double omega) {
+  std::vector<gf_ctx*> by[2];
+  for (gf_ctx* c : members) by[c->fp64 ? 1 : 0].push_back(c);
+  for (int p = 0; p < 2; ++p)
+    for (int f = 0; f < 2; ++f) {
+      if (by[f].empty()) continue;
+      int r = f ? group_half_t<double>(by[f], omega, p) : group_half_t<float>(by[f], omega, p);
+      if (r) return r;
+    }
+  for (gf_ctx* c : members) {
+    c->sweep_index++;
+    if (c->prec == GF_MIXED && !c->fp64) c->dirty = true;
+  }
+  return GF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1157,6 +1225,131 @@ int gf_slab_pack(gf_ctx* c, int slice, int parity, void* buf) { return slab_copy
 
 int gf_slab_unpack(gf_ctx* c, int slice, int parity, const void* buf) {
   return slab_copy(c, slice, parity, const_cast<void*>(buf), false);
+}
+
+int gf_group_sweep(gf_ctx* const* ctxs, int n, gf_algo algo, double param, int n_sweeps) {
+  int r = check_group(ctxs, n);
+  if (r) return r;
+  if (algo != GF_OR && algo != GF_RELAX) return fail(GF_EINVAL, "group sweeps run GF_OR or GF_RELAX");
+  if ((r = check_algo_param(algo, param))) return r;
+  if (n_sweeps < 0) return fail(GF_EINVAL, "n_sweeps < 0");
+  std::vector<gf_ctx*> m(ctxs, ctxs + n);
+  const double omega = algo == GF_RELAX ? 1.0 : param;
+  for (int k = 0; k < n_sweeps; ++k)
+    if ((r = group_sweep_once(m, omega))) return r;
+  for (gf_ctx* c : m) {
+    if ((r = sync_master(c))) return r;
+    GF_CUDA(cudaStreamSynchronize(c->st));
+  }
+  return GF_OK;
+}
+
+int gf_group_fix(gf_ctx* const* ctxs, int n, const gf_fix_params* P, gf_fix_result* results) {
+  int r = check_group(ctxs, n);
+  if (r) return r;
+  if (!P) return fail(GF_EINVAL, "params is NULL");
+  if (P->algo != GF_OR && P->algo != GF_RELAX) return fail(GF_EINVAL, "gf_group_fix runs GF_OR or GF_RELAX");
+  if ((r = check_algo_param(P->algo, P->param))) return r;
+  if (!(P->theta_target > 0) || P->max_sweeps < 0 || P->check_interval < 1 || P->reunit_interval < 0)
+    return fail(GF_EINVAL, "bad fix parameters");
+  Range range_fix("gf_group_fix");
+  const auto t_start = std::chrono::steady_clock::now();
+  const double omega = P->algo == GF_RELAX ? 1.0 : P->param;
+  std::vector<gf_fix_result> R(n);
+  std::vector<int> since(n, 0);
+  std::vector<int> live(n, 1);
+  std::vector<double> ct;
+  for (auto& x : R) memset(&x, 0, sizeof x);
+  for (;;) {
+    // every live member: theta per unit (a copy, or a Coulomb time-slice) from the standalone pass
+    std::vector<gf_ctx*> sweepers;
+    for (int k = 0; k < n; ++k) {
+      if (!live[k]) continue;
+      gf_ctx* c = ctxs[k];
+      if ((r = observables(c, ct))) return r;
+      R[k].checks++;
+      const int Nt = c->dims[0];
+      const bool coul = c->gauge == GF_COULOMB;
+      const bool final_phase = c->fp64 || c->prec == GF_FP32;
+      double worst = 0, fs = 0, tmax = 0;
+      int n_active = 0;
+      for (int q = 0; q < c->ncopies; ++q) {
+        double tsum = 0;
+        for (int t = 0; t < Nt; ++t) {
+          fs += ct[2 * ((size_t)q * Nt + t)];
+          tsum += ct[2 * ((size_t)q * Nt + t) + 1];
+        }
+        for (int u = 0; u < (coul ? Nt : 1); ++u) {
+          const double th = coul ? ct[2 * ((size_t)q * Nt + u) + 1] : tsum / Nt;
+          tmax = std::max(tmax, th);
+          const int v = (final_phase && th < P->theta_target) ? 0 : 1;
+          if (coul) c->active_h[(size_t)q * Nt + u] = v;
+          else
+            for (int t = 0; t < Nt; ++t) c->active_h[(size_t)q * Nt + t] = v;
+          if (v) {
+            n_active++;
+            worst = std::max(worst, th);
+          }
+        }
+      }
+      R[k].F_mean = fs / ((double)c->ncopies * Nt);
+      R[k].theta_max = tmax;
+      if ((r = upload_active(c))) return r;
+      if (n_active == 0) {
+        R[k].converged = 1;
+        live[k] = 0;
+        continue;
+      }
+      if (R[k].sweeps >= P->max_sweeps) {
+        live[k] = 0;
+        continue;
+      }
+      if (!c->fp64 && c->prec == GF_MIXED && (worst < P->switch_theta || !std::isfinite(worst))) {
+        if ((r = promote(c))) return r;
+        continue;  // evaluated again in FP64 at the next round
+      }
+      sweepers.push_back(c);
+      R[k].site_updates += (uint64_t)std::min(P->check_interval, P->max_sweeps - R[k].sweeps) * n_active *
+                           (coul ? c->G.V3 : c->G.V);
+    }
+    if (sweepers.empty()) {
+      bool any = false;
+      for (int k = 0; k < n; ++k) any = any || live[k];
+      if (!any) break;
+      continue;  // only promotions this round
+    }
+    // a common interval: the members that are still sweeping
+    int steps = P->check_interval;
+    for (int k = 0; k < n; ++k)
+      if (live[k]) steps = std::min(steps, std::max(1, P->max_sweeps - R[k].sweeps));
+    for (int s = 0; s < steps; ++s) {
+      if ((r = group_sweep_once(sweepers, omega))) return r;
+      for (int k = 0; k < n; ++k) {
+        if (!live[k] || std::find(sweepers.begin(), sweepers.end(), ctxs[k]) == sweepers.end()) continue;
+        gf_ctx* c = ctxs[k];
+        if (c->fp64) R[k].sweeps_fp64++;
+        else R[k].sweeps_fp32++;
+        R[k].sweeps++;
+        if (P->reunit_interval > 0 && ++since[k] >= P->reunit_interval) {
+          since[k] = 0;
+          if ((r = reunitarize(c))) return r;
+        }
+      }
+    }
+  }
+  bool all = true;
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  for (int k = 0; k < n; ++k) {
+    gf_ctx* c = ctxs[k];
+    std::fill(c->active_h.begin(), c->active_h.end(), 1);
+    if ((r = upload_active(c))) return r;
+    if ((r = sync_master(c))) return r;
+    R[k].seconds = secs;
+    all = all && R[k].converged;
+    if (results) results[k] = R[k];
+  }
+  if (!all) return fail(GF_ENOTCONV, "some group members did not reach theta_target");
+  return GF_OK;
 }
 
 int gf_set_fused_observables(gf_ctx* c, int on) {

@@ -15,6 +15,12 @@ cudaError_t launch_sweep(const SweepArgs<R>& a, int gauge, int algo, int lpt, cu
 // FP32 storage with Step 1 in FP64 (GF_MP).
 cudaError_t launch_sweep_mp(const SweepArgs<float>& a, int gauge, int algo, int lpt, cudaStream_t st);
 
+// One half-sweep (overrelaxation) of several lattices in one launch.
+template <typename R>
+struct GroupArgs;
+template <typename R>
+cudaError_t launch_group(const GroupArgs<R>& g, int gauge, int lpt, cudaStream_t st);
+
 // Exact F/theta per (copy, slice) into out[ct][2] (device).
 template <typename R>
 cudaError_t launch_observables(const void* links, const Geom& G, int NS, int gauge, uint32_t ncopies,

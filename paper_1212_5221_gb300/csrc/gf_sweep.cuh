@@ -972,4 +972,44 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R, GAUGE, LPT, MP>()) sweep_
   }
 }
 
+// ---------------------------------------------------------------------------
+// Several lattices of different extents (the same gauge and storage) in one
+// persistent launch: the tiles of every member are numbered one after the
+// other and a block finds the member of a tile by binary search of the
+// members' cumulative tile counts.  The members' arguments travel in the
+// kernel's parameter space (__grid_constant__, read in place).
+constexpr int GROUP_MAX = 48;
+
+template <typename R>
+struct GroupArgs {
+  SweepArgs<R> m[GROUP_MAX];
+  uint64_t tile_end[GROUP_MAX];  // tiles of members 0..k
+  uint32_t n;
+  uint64_t ntiles;
+};
+
+template <typename R, int GAUGE, int ALGO, int LPT>
+__global__ void __launch_bounds__(BLOCK, min_blocks<R, GAUGE, LPT>())
+    sweep_group_kernel(const __grid_constant__ GroupArgs<R> g) {
+  constexpr int L = 8 / LPT;
+  constexpr uint32_t TILE = BLOCK / L;
+  const int lane = (int)(threadIdx.x % L);
+  const uint32_t local = threadIdx.x / L;
+  for (uint64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+    uint32_t lo = 0, hi = g.n - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (tile < g.tile_end[mid]) hi = mid;
+      else lo = mid + 1;
+    }
+    const SweepArgs<R>& a = g.m[lo];
+    const uint64_t t = tile - (lo ? g.tile_end[lo - 1] : 0);
+    const uint32_t Vh = a.geom.Vh;
+    const uint32_t tiles_per_copy = (Vh + TILE - 1) / TILE;
+    const uint32_t copy = (uint32_t)(t / tiles_per_copy);
+    const uint32_t sp0 = (uint32_t)(t - (uint64_t)copy * tiles_per_copy) * TILE;
+    site_dispatch<R, GAUGE, ALGO, LPT, false, false>(a, copy, sp0 + local, sp0 + local < Vh, lane, nullptr, sp0);
+  }
+}
+
 }  // namespace gfk

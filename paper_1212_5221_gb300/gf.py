@@ -117,6 +117,8 @@ _SIG = {
     "gf_set_sa_micro": [_P, _I],
     "gf_set_sa_trace": [_P, _P],
     "gf_set_slab": [_P, _I, _I],
+    "gf_group_sweep": [_P, _I, _I, ctypes.c_double, _I],
+    "gf_group_fix": [_P, _I, ctypes.POINTER(gf_fix_params), _P],
     "gf_sweep_half": [_P, _I, ctypes.c_double, _I, _I, ctypes.c_uint64],
     "gf_slab_bytes": [_P, ctypes.POINTER(ctypes.c_size_t)],
     "gf_slab_pack": [_P, _I, _I, _P],
@@ -394,6 +396,31 @@ def gf_set_sa_trace(h, device_ptr):
 
 
 GF_SLAB_OWNED, GF_SLAB_BOUNDARY, GF_SLAB_INNER = 0, 1, 2
+GF_GROUP_MAX = 48
+
+
+def _group(handles):
+    arr = (_P * len(handles))(*handles)
+    return arr, len(handles)
+
+
+def gf_group_sweep(handles, algo="or", param=1.7, n_sweeps=1):
+    """n_sweeps sweeps of every context in `handles` (any extents, one gauge), one launch per half-sweep."""
+    arr, n = _group(handles)
+    _check(lib().gf_group_sweep(arr, n, _enum(algo, ALGOS), float(param), int(n_sweeps)), "gf_group_sweep")
+
+
+def gf_group_fix(handles, algo="or", param=1.7, theta_target=1e-12, max_sweeps=100000, check_interval=10,
+                 reunit_interval=100, switch_theta=1e-8, raise_on_notconv=True):
+    """gf_fix of every context in `handles`, sharing the sweep launches; a list of result dicts."""
+    arr, n = _group(handles)
+    p = gf_fix_params(_enum(algo, ALGOS), float(param), float(theta_target), int(max_sweeps),
+                      int(check_interval), int(reunit_interval), float(switch_theta), 0)
+    res = (gf_fix_result * n)()
+    st = lib().gf_group_fix(arr, n, ctypes.byref(p), res)
+    if not (st == GF_ENOTCONV and not raise_on_notconv):
+        _check(st, "gf_group_fix")
+    return [res[k].as_dict() for k in range(n)]
 
 
 def gf_set_slab(h, t0, Nt_global):
