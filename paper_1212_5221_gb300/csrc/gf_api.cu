@@ -1258,6 +1258,7 @@ int gf_group_fix(gf_ctx* const* ctxs, int n, const gf_fix_params* P, gf_fix_resu
   std::vector<gf_fix_result> R(n);
   std::vector<int> since(n, 0);
   std::vector<int> live(n, 1);
+  std::vector<uint64_t> units(n, 0);  // sites of a member's active units
   std::vector<double> ct;
   for (auto& x : R) memset(&x, 0, sizeof x);
   for (;;) {
@@ -1309,8 +1310,7 @@ int gf_group_fix(gf_ctx* const* ctxs, int n, const gf_fix_params* P, gf_fix_resu
         continue;  // evaluated again in FP64 at the next round
       }
       sweepers.push_back(c);
-      R[k].site_updates += (uint64_t)std::min(P->check_interval, P->max_sweeps - R[k].sweeps) * n_active *
-                           (coul ? c->G.V3 : c->G.V);
+      units[k] = (uint64_t)n_active * (coul ? c->G.V3 : c->G.V);
     }
     if (sweepers.empty()) {
       bool any = false;
@@ -1330,6 +1330,7 @@ int gf_group_fix(gf_ctx* const* ctxs, int n, const gf_fix_params* P, gf_fix_resu
         if (c->fp64) R[k].sweeps_fp64++;
         else R[k].sweeps_fp32++;
         R[k].sweeps++;
+        R[k].site_updates += units[k];
         if (P->reunit_interval > 0 && ++since[k] >= P->reunit_interval) {
           since[k] = 0;
           if ((r = reunitarize(c))) return r;
