@@ -557,7 +557,8 @@ def gf_server_submit(s, dims, gauge="landau", prec="mixed", host_links=None, orb
     j.host_out = None if host_out is None else _links_arg(host_out)
     j.tag = int(tag)
     if anneal:
-        a = dict(sa_steps=0, T_start=1.45, T_end=0.01, sr_sweeps=0, sr_p=0.5, sr_theta=0.0, seed=0, **anneal)
+        a = dict(sa_steps=0, T_start=1.45, T_end=0.01, sr_sweeps=0, sr_p=0.5, sr_theta=0.0, seed=0)
+        a.update(anneal)
         j.anneal = 1
         j.protocol = gf_protocol_params(int(a["sa_steps"]), float(a["T_start"]), float(a["T_end"]),
                                         int(a["sr_sweeps"]), float(a["sr_p"]), float(a["sr_theta"]),
@@ -602,6 +603,9 @@ def gf_philox(seed, counters):
     return out
 
 
+_CUDA_STREAM_LEGACY = 0x1  # the CUDA runtime's handle of the legacy default stream
+
+
 class GaugeField:
     """A context whose device memory and stream are PyTorch's.
 
@@ -620,7 +624,11 @@ class GaugeField:
         ptr = self.buffer.data_ptr()
         aligned = (ptr + 255) // 256 * 256
         self.stream = stream if stream is not None else torch.cuda.Stream(dev)
-        self.h = gf_create_ext(self.dims, self.n_copies, gauge, prec, _P(self.stream.cuda_stream), aligned,
+        # torch's default stream has the handle 0, which the C ABI reads as "create a
+        # stream of your own": pass the legacy default stream's handle instead, so
+        # that the library's work and torch's are ordered on the same stream
+        handle = self.stream.cuda_stream or _CUDA_STREAM_LEGACY
+        self.h = gf_create_ext(self.dims, self.n_copies, gauge, prec, _P(handle), aligned,
                                nbytes + 256 - (aligned - ptr))
 
     def close(self):

@@ -22,9 +22,10 @@ slices, reduced over the processes in FP64.
 Everything device-side (the half-sweeps, packing the messages, the slice
 observables) is libgf's; this module only sequences those calls and moves
 the buffers with torch.distributed (NCCL for device buffers, gloo on CPU).
-The schedule talks to a `backend` with five methods -- half(algo, param,
-parity, part, seed), pack(slice, parity), unpack(slice, parity, buf),
-slice_observables(), advance() -- so the same schedule drives a GPU slab
+The schedule talks to a `backend` with the methods half(algo, param, parity,
+part, seed), pack(slice, parity), unpack(slice, parity, buf),
+slice_observables(), advance(), reunitarize() and stream_context() (the
+stream the messages are ordered on), so the same schedule drives a GPU slab
 (`GpuSlab`) or any other implementation of those steps.
 """
 from __future__ import annotations
@@ -117,12 +118,15 @@ class TimeSlab:
 
     def half(self, algo, param, p, seed=0):
         b, nt = self.b, self.nt
-        b.half(algo, param, p, BOUNDARY, seed)
-        handle = self.ring.start(b.pack(0, 1 - p), b.pack(nt, p))
-        b.half(algo, param, p, INNER, seed)
-        from_prev, from_next = self.ring.finish(handle)
-        b.unpack(0, p, from_prev)
-        b.unpack(nt, 1 - p, from_next)
+        # the messages' buffers, copies and point-to-point operations are
+        # ordered on the backend's stream, behind the half-sweeps
+        with b.stream_context():
+            b.half(algo, param, p, BOUNDARY, seed)
+            handle = self.ring.start(b.pack(0, 1 - p), b.pack(nt, p))
+            b.half(algo, param, p, INNER, seed)
+            from_prev, from_next = self.ring.finish(handle)
+            b.unpack(0, p, from_prev)
+            b.unpack(nt, 1 - p, from_next)
 
     def sweep(self, algo, param, n_sweeps=1, seed=0):
         """n checkerboard sweeps (even half, then odd) of the whole lattice."""
@@ -171,11 +175,11 @@ class GpuSlab:
         self.torch = torch
         self.dims = (nt + 2,) + tuple(dims_global[1:])
         self.t0, self.nt = t0, nt
-        # the current stream by default, so that the boundary messages, which
-        # torch.distributed orders against the current stream, follow the
-        # half-sweeps and copies libgf enqueues
-        self.field = gf.GaugeField(self.dims, gauge, prec,
-                                   stream=stream if stream is not None else torch.cuda.current_stream())
+        # one stream for the library's work and for the messages: the schedule
+        # makes it current around each half-sweep, so torch.distributed orders
+        # the boundary messages behind the half-sweeps and copies libgf enqueues
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.field = gf.GaugeField(self.dims, gauge, prec, stream=self.stream)
         self.h = self.field.h
         gf.gf_set_slab(self.h, t0, dims_global[0])
         self.msg_bytes = gf.gf_slab_bytes(self.h)
@@ -192,8 +196,12 @@ class GpuSlab:
     def half(self, algo, param, parity, part, seed):
         gf.gf_sweep_half(self.h, algo, param, parity, part, seed)
 
+    def stream_context(self):
+        return self.torch.cuda.stream(self.stream)
+
     def pack(self, slice_, parity):
-        buf = self.torch.empty(self.msg_bytes, dtype=self.torch.uint8, device="cuda")
+        with self.torch.cuda.stream(self.stream):
+            buf = self.torch.empty(self.msg_bytes, dtype=self.torch.uint8, device="cuda")
         gf.gf_slab_pack(self.h, slice_, parity, buf.data_ptr())
         return buf
 

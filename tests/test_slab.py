@@ -64,6 +64,11 @@ class OracleSlab:
     def advance(self):
         self.sweep_index += 1
 
+    def stream_context(self):
+        import contextlib
+
+        return contextlib.nullcontext()
+
     def reunitarize(self):
         self.orc.reunitarize(self.U)
 
