@@ -450,8 +450,10 @@ int gf_functional_theta_noalloc(const int dims[4], gf_gauge gauge, const double*
  * members' streams are ordered before and after it with events.  Small
  * lattices, whose own launches would leave most of the GPU idle, fill it
  * together.  The paper has no counterpart (its batching is over time-slices
- * of one lattice); each member's links come out exactly as if it had been
- * swept alone with the same links-per-thread.
+ * of one lattice); each member's links come out as if it had been swept
+ * alone with the same links-per-thread: bit for bit in FP64 and in the
+ * Landau/Coulomb form, to FP32 rounding for FP32 MAG (two separately compiled
+ * kernels).
  * gf_group_sweep: n_sweeps sweeps of GF_OR (omega = param) or GF_RELAX, then
  * GF_MIXED members' FP64 masters are brought up to date; synchronous. */
 #define GF_GROUP_MAX 48

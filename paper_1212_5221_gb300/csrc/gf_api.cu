@@ -778,8 +778,9 @@ int group_half_t(const std::vector<gf_ctx*>& m, double omega, int parity) {
   static thread_local gfk::GroupArgs<R> g;
   uint64_t cum = 0;
   for (size_t k = 0; k < m.size(); ++k) {
-    fill_args(g.m[k], m[k], gfk::ALG_OR, omega, parity, 0, (uint32_t)m[k]->sweep_index, 0, 1, GF_PREFETCH_NONE,
-              nullptr);
+    // the group kernel prefetches the next tile into L2 or nothing (it has no staged form)
+    fill_args(g.m[k], m[k], gfk::ALG_OR, omega, parity, 0, (uint32_t)m[k]->sweep_index, 0, 1,
+              m[k]->prefetch == GF_PREFETCH_NONE ? GF_PREFETCH_NONE : GF_PREFETCH_L2, nullptr);
     cum += (uint64_t)((m[k]->G.Vh + tile - 1) / tile) * (uint64_t)m[k]->ncopies;
     g.tile_end[k] = cum;
   }

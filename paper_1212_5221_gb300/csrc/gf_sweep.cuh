@@ -988,22 +988,53 @@ struct GroupArgs {
   uint64_t ntiles;
 };
 
+template <typename R>
+__device__ __forceinline__ uint32_t group_member(const GroupArgs<R>& g, uint64_t tile) {
+  uint32_t lo = 0, hi = g.n - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (tile < g.tile_end[mid]) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
 template <typename R, int GAUGE, int ALGO, int LPT>
 __global__ void __launch_bounds__(BLOCK, min_blocks<R, GAUGE, LPT>())
     sweep_group_kernel(const __grid_constant__ GroupArgs<R> g) {
+  constexpr int NC = store_traits<R>::NC;
   constexpr int L = 8 / LPT;
   constexpr uint32_t TILE = BLOCK / L;
+  constexpr int WORDS = (int)(sizeof(SweepArgs<R>) / 4);
+  static_assert(sizeof(SweepArgs<R>) % 4 == 0 && WORDS <= BLOCK, "arguments copied word by word");
+  // the current member's arguments, copied to shared memory when the member changes
+  __shared__ __align__(16) SweepArgs<R> cur;
   const int lane = (int)(threadIdx.x % L);
   const uint32_t local = threadIdx.x / L;
+  uint32_t held = 0xffffffffu;
   for (uint64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
-    uint32_t lo = 0, hi = g.n - 1;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (tile < g.tile_end[mid]) hi = mid;
-      else lo = mid + 1;
+    const uint32_t m = group_member(g, tile);
+    if (m != held) {
+      __syncthreads();  // every thread is done with the previous member's arguments
+      if (threadIdx.x < WORDS)
+        reinterpret_cast<uint32_t*>(&cur)[threadIdx.x] = reinterpret_cast<const uint32_t*>(&g.m[m])[threadIdx.x];
+      __syncthreads();
+      held = m;
     }
-    const SweepArgs<R>& a = g.m[lo];
-    const uint64_t t = tile - (lo ? g.tile_end[lo - 1] : 0);
+    const uint64_t next = tile + gridDim.x;
+    if (next < g.ntiles && threadIdx.x < 9 * NC) {  // the next tile into L2, as the single-lattice kernel
+      const uint32_t mn = group_member(g, next);
+      const SweepArgs<R>& an = g.m[mn];
+      if (an.prefetch) {
+        const uint64_t tn = next - (mn ? g.tile_end[mn - 1] : 0);
+        const uint32_t tpc = (an.geom.Vh + TILE - 1) / TILE;
+        const uint32_t cn = (uint32_t)(tn / tpc);
+        const uint32_t sn = (uint32_t)(tn - (uint64_t)cn * tpc) * TILE;
+        prefetch_tile<R, GAUGE>(an, cn, sn, min(TILE, an.geom.Vh - sn), (int)threadIdx.x);
+      }
+    }
+    const SweepArgs<R>& a = cur;
+    const uint64_t t = tile - (m ? g.tile_end[m - 1] : 0);
     const uint32_t Vh = a.geom.Vh;
     const uint32_t tiles_per_copy = (Vh + TILE - 1) / TILE;
     const uint32_t copy = (uint32_t)(t / tiles_per_copy);

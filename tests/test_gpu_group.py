@@ -61,7 +61,10 @@ def test_group_sweep_equals_alone(gf, synth, orc, gauge, prec):
             gf.gf_store_links(h, 0, V)
         finally:
             gf.gf_destroy(h)
-        assert np.array_equal(got[k], V), (k, np.abs(got[k] - V).max())
+        if prec == "fp64" or gauge != "mag":
+            assert np.array_equal(got[k], V), (k, np.abs(got[k] - V).max())
+        else:  # the FP32 MAG form of two separately compiled kernels rounds alike only to FP32 rounding
+            assert np.abs(got[k] - V).max() <= 2e-5, (k, np.abs(got[k] - V).max())
         if prec == "fp64":
             W = U.copy()
             orc.sweep(W, gauge, "or", 1.7, 3)
