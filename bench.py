@@ -860,17 +860,23 @@ def run_group_study(args):
 def run_kernel_target(args):
     """Short, fixed launch sequences on the workload's lattice for ncu captures.
     fp32 / fp64 / mixed: 3 sweeps in that precision (mixed: FP32 sweeps that
-    accumulate g).  window: a bounded slice of one bench step -- 100 mixed
-    FP32 sweeps with theta checks every 20 and a master sync at 100, the switch
-    to the FP64 master, and 60 FP64 sweeps with checks."""
+    accumulate g); mag64 / mag32: the same in MAG gauge (omega 1.35) in FP64 /
+    GF_MIXED storage; check32: 3 mixed FP32 sweeps of which the last sums F
+    and theta (the fused check) and the read-only pass over the even sites.
+    window: a bounded slice of one bench step -- 100 mixed FP32 sweeps with
+    theta checks every 20 and a master sync at 100, the switch to the FP64
+    master, and 60 FP64 sweeps with checks."""
     from paper_1212_5221_gb300 import build, gf, inputs
 
     build.build_all()
     W = WORKLOAD
     dims = W["dims"]
     U = inputs.links(dims, "smooth", W["eps"], W["field_seed"])
-    prec = "mixed" if args.kernel_target == "window" else args.kernel_target
-    h = gf.gf_create(dims, W["gauge"], prec)
+    kt = args.kernel_target
+    prec = {"window": "mixed", "mag64": "fp64", "mag32": "mixed", "check32": "mixed"}.get(kt, kt)
+    gauge = "mag" if kt.startswith("mag") else W["gauge"]
+    omega = 1.35 if gauge == "mag" else W["omega"]
+    h = gf.gf_create(dims, gauge, prec)
     gf.gf_load_links(h, 0, U)
     gf.gf_random_gauge_transform(h, 1000)
     if args.kernel_target == "window":
@@ -879,8 +885,11 @@ def run_kernel_target(args):
         gf.gf_fix(h, max_sweeps=100, **kw)
         gf.gf_promote(h)
         gf.gf_fix(h, max_sweeps=60, **kw)
+    elif kt == "check32":
+        gf.gf_fix(h, "or", omega, 1e-30, max_sweeps=3, check_interval=3, reunit_interval=0,
+                  switch_theta=1e-40, raise_on_notconv=False)
     else:
-        gf.gf_sweep(h, "or", W["omega"], 3, observables=False)
+        gf.gf_sweep(h, "or", omega, 3, observables=False)
     F, T = gf.gf_functional_theta(h)
     gf.gf_destroy(h)
     print(json.dumps({"kernel_target": args.kernel_target, "F": float(F[0]), "theta": float(T[0])}))
@@ -903,7 +912,8 @@ def main():
                     help="plain-FP64 runs on the orbit seeds of the first timed steps (time-to-theta ratio)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-fp64-baseline", dest="fp64_baseline", action="store_false")
-    ap.add_argument("--kernel-target", choices=["fp32", "fp64", "mixed", "window"], default=None,
+    ap.add_argument("--kernel-target", choices=["fp32", "fp64", "mixed", "window", "mag64", "mag32", "check32"],
+                    default=None,
                     help="only run a short, fixed launch sequence of the workload (for ncu)")
     ap.add_argument("--serving", action="store_true", help="run the serving workload (job p50/p99)")
     ap.add_argument("--serve-jobs", type=int, default=2000)
