@@ -84,15 +84,15 @@ def _free_port():
         return s.getsockname()[1]
 
 
-DIMS = (8, 4, 4, 6)
+DIMS = (12, 4, 4, 6)
 
 
-def _field(gauge):
+def _field(gauge, dims=DIMS):
     import oracle
     from paper_1212_5221_gb300 import inputs
 
     inputs.build()
-    U = inputs.links(DIMS, "smooth", 0.4, 5)
+    U = inputs.links(dims, "smooth", 0.4, 5)
     oracle.random_gauge_transform(U, 17)
     return U
 
@@ -126,9 +126,11 @@ def _worker(rank, world, port, gauge, q):
         dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("world", [2, 3])
 @pytest.mark.parametrize("gauge", ["landau", "mag"])
-def test_two_process_slabs_equal_whole_lattice(orc, synth, gauge):
-    world = 2
+def test_process_slabs_equal_whole_lattice(orc, synth, gauge, world):
+    """Two processes (each the other's previous and next) and three (distinct
+    neighbours) against the whole lattice."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
