@@ -1,0 +1,50 @@
+"""Parity on the bench's own workload: the 32^3 x 64 Landau lattice
+(eps = 0.35 field seed 1, the orbit point of Haar seed 1000 that the first
+timed step starts from), in the launch configurations the bench times.
+
+One sweep of all 2,097,152 sites is within the oracle's reach, so every link
+is compared, not a sample: FP64 storage with eight links per lane (the
+bench's FP64 kernel) to 1e-12, and the mixed-precision FP32 stage with four
+links per lane and the site accumulator, read back through the FP64 master
+it moves, to the FP32 single-sweep bound."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (64, 32, 32, 32)
+
+
+@pytest.fixture(scope="module")
+def field():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import oracle
+    from paper_1212_5221_gb300 import build, inputs
+
+    build.build_all()
+    oracle.build()
+    U = inputs.links(DIMS, "smooth", 0.35, 1)
+    oracle.random_gauge_transform(U, 1000)
+    W = U.copy()
+    oracle.sweep(W, "landau", "or", 1.7, 1)
+    return U, W
+
+
+@pytest.mark.parametrize("prec,lpt,tol", [("fp64", 8, 1e-12), ("mixed", 4, 2e-5)])
+def test_bench_workload_single_sweep(field, prec, lpt, tol):
+    from paper_1212_5221_gb300 import gf
+
+    U, W = field
+    h = gf.gf_create(DIMS, "landau", prec)
+    try:
+        gf.gf_set_links_per_thread(h, lpt)
+        gf.gf_load_links(h, 0, U)
+        gf.gf_sweep(h, "or", 1.7, 1, observables=False)
+        V = np.empty_like(U)
+        gf.gf_store_links(h, 0, V)
+    finally:
+        gf.gf_destroy(h)
+    err = np.abs(V - W).max()
+    assert err <= tol, err
