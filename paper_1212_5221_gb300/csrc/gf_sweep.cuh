@@ -959,16 +959,41 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R, GAUGE, LPT, MP>()) sweep_
   const uint64_t ntiles = (uint64_t)tiles_per_copy * a.ncopies;
   const int lane = (int)(threadIdx.x % L);
   const uint32_t local = threadIdx.x / L;
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const uint64_t next = tile + gridDim.x;
-    if (a.prefetch && next < ntiles && threadIdx.x < 9 * NC) {
-      const uint32_t nc = (uint32_t)(next / tiles_per_copy);
-      const uint32_t nsp0 = (uint32_t)(next - (uint64_t)nc * tiles_per_copy) * TILE;
-      prefetch_tile<R, GAUGE>(a, nc, nsp0, min(TILE, Vh - nsp0), (int)threadIdx.x);
+  if constexpr (sizeof(R) == 8) {
+    // FP64 is ALU-bound: every block takes an equal contiguous range of the
+    // (copy, site) indices in tiles of TILE, so that no SM finishes a whole
+    // tile before the others (whole tiles dealt round-robin left a 4 % tail)
+    const uint64_t total = (uint64_t)Vh * a.ncopies;
+    const uint64_t lo = total * blockIdx.x / gridDim.x, hi = total * (blockIdx.x + 1) / gridDim.x;
+    // (copy, site) of the tile's first index, advanced by TILE per iteration
+    uint32_t c0 = (uint32_t)(lo / Vh), s0 = (uint32_t)(lo - (uint64_t)c0 * Vh);
+    for (uint64_t base = lo; base < hi; base += TILE) {
+      if (a.prefetch && base + TILE < hi && threadIdx.x < 9 * NC) {
+        uint32_t nc = c0, ns = s0 + TILE;
+        while (ns >= Vh) ns -= Vh, ++nc;
+        const uint32_t n = (uint32_t)min((uint64_t)min(TILE, Vh - ns), hi - base - TILE);
+        prefetch_tile<R, GAUGE>(a, nc, ns, n, (int)threadIdx.x);
+      }
+      uint32_t copy = c0, sp = s0 + local;
+      while (sp >= Vh) sp -= Vh, ++copy;
+      site_dispatch<R, GAUGE, ALGO, LPT, OBS, MP>(a, copy, sp, base + local < hi, lane, nullptr, sp);
+      s0 += TILE;
+      while (s0 >= Vh) s0 -= Vh, ++c0;
     }
-    const uint32_t copy = (uint32_t)(tile / tiles_per_copy);
-    const uint32_t sp0 = (uint32_t)(tile - (uint64_t)copy * tiles_per_copy) * TILE;
-    site_dispatch<R, GAUGE, ALGO, LPT, OBS, MP>(a, copy, sp0 + local, sp0 + local < Vh, lane, nullptr, sp0);
+  } else {
+    // FP32 is HBM-bound: whole tiles dealt round-robin keep the blocks' reads
+    // within one window of the arrays at a time
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const uint64_t next = tile + gridDim.x;
+      if (a.prefetch && next < ntiles && threadIdx.x < 9 * NC) {
+        const uint32_t nc = (uint32_t)(next / tiles_per_copy);
+        const uint32_t nsp0 = (uint32_t)(next - (uint64_t)nc * tiles_per_copy) * TILE;
+        prefetch_tile<R, GAUGE>(a, nc, nsp0, min(TILE, Vh - nsp0), (int)threadIdx.x);
+      }
+      const uint32_t copy = (uint32_t)(tile / tiles_per_copy);
+      const uint32_t sp0 = (uint32_t)(tile - (uint64_t)copy * tiles_per_copy) * TILE;
+      site_dispatch<R, GAUGE, ALGO, LPT, OBS, MP>(a, copy, sp0 + local, sp0 + local < Vh, lane, nullptr, sp0);
+    }
   }
 }
 
