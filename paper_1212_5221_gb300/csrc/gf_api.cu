@@ -264,7 +264,10 @@ void prof_collect(gf_ctx* c) {
 int default_lpt(const gf_ctx* c, int algo) {
   int v = c->lpt[c->fp64][algo];
   if (v) return v;
-  return c->fp64 ? 8 : 4;  // fastest on GB300 for the 32^3 x 64 Landau sweep
+  // fastest on GB300 for the 32^3 x 64 Landau sweep: FP64 (and GF_MP, whose
+  // Step 1 is FP64) with one lane per site, so that no lane repeats Step 1;
+  // FP32 with two lanes per site
+  return (c->fp64 || c->prec == GF_MP) ? 8 : 4;
 }
 
 // The kernel arguments of one half-sweep of context c.
