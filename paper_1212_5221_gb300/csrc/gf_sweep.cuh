@@ -218,6 +218,13 @@ constexpr size_t stage_smem_bytes() {
   return 2 * StageGeom<BLOCK / (8 / LPT)>::BYTES + 16;
 }
 
+// Dynamic shared memory of the non-staged FP32 sweep with GF_MIXED's
+// accumulator: the three vectors of every site of a tile.
+template <int LPT>
+constexpr size_t acc_smem_bytes() {
+  return (size_t)3 * (BLOCK / (8 / LPT)) * 16;
+}
+
 __device__ __forceinline__ void stage_range(const Geom& G, uint32_t sp0, uint32_t tile, int k, int64_t& lo,
                                             uint32_t& clo, uint32_t& chi) {
   int64_t ext = tile;
@@ -690,6 +697,25 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
     off[j] = link_off(copy, par, slot, a.NS, NC, Vh, ssp);
   }
 
+  // GF_MIXED: the site's accumulated transformation is needed only after Step
+  // 1; lane 0 starts copying its three vectors into shared memory now
+  // (cp.async, no registers held), so that the load overlaps the gather
+  // (the launch gives the non-staged kernel 3 x TILE x 16 bytes of dynamic
+  // shared memory for this when the accumulator is in use)
+  constexpr bool ACC_ASYNC = sizeof(R) == 4 && GAUGE != COULOMB && !OBS;
+  extern __shared__ __align__(128) unsigned char stage_smem[];
+  float4* const acc_stage = reinterpret_cast<float4*>(stage_smem);
+  const bool acc_async = ACC_ASYNC && a.acc && valid && lane == 0 && stage == nullptr;
+  if (acc_async) {
+    const float4* src = reinterpret_cast<const float4*>(a.links) + link_off(copy, a.parity, 4, a.NS, NC, Vh, sp);
+    const uint32_t dst = smem_u32(&acc_stage[3 * (threadIdx.x / L)]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16u * k), "l"(src + (size_t)k * Vh)
+                   : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+
   // gather: K = sum of U_mu(x) and U_mu(x - mu)^dag over the lane's slots
   __shared__ cx<R> row2c[ROW2C ? 12 * BLOCK : 1];
   cx<R>* const r2c = row2c + (ROW2C ? threadIdx.x : 0);  // this thread's column: [up-link][entry] stride BLOCK
@@ -807,7 +833,19 @@ __device__ __forceinline__ void sweep_site_k(const SweepArgs<R>& a, uint32_t cop
   if (CAN_ACC && a.acc && valid && lane == 0) {
     const size_t acc_off = link_off(copy, a.parity, 4, a.NS, NC, Vh, sp);
     mat3<R> t, n;
-    load_slot<R, TILE>(stage, Gm, sp0, 8, sp, a.links + acc_off, Vh, t);
+    if (acc_async) {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      const float4* q = &acc_stage[3 * (threadIdx.x / L)];
+      const float4 x = q[0], y = q[1], z = q[2];
+      t.e[0][0] = {(R)x.x, (R)x.y};
+      t.e[0][1] = {(R)x.z, (R)x.w};
+      t.e[0][2] = {(R)y.x, (R)y.y};
+      t.e[1][0] = {(R)y.z, (R)y.w};
+      t.e[1][1] = {(R)z.x, (R)z.y};
+      t.e[1][2] = {(R)z.z, (R)z.w};
+    } else {
+      load_slot<R, TILE>(stage, Gm, sp0, 8, sp, a.links + acc_off, Vh, t);
+    }
     reproject_rows(t);
     reconstruct_row2(t);
     apply_left(G, t, n);

@@ -16,14 +16,18 @@ static cudaError_t launch_g(const GroupArgs<R>& g, cudaStream_t st) {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, BLOCK, 0) != cudaSuccess || per_sm < 1) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, BLOCK,
+                                                      sizeof(R) == 4 ? acc_smem_bytes<LPT>() : 0) != cudaSuccess ||
+        per_sm < 1) {
       cudaGetLastError();
       return 0u;
     }
     return (unsigned)(sms * per_sm);
   }();
   const unsigned blocks = (unsigned)((resident && g.ntiles > resident) ? resident : g.ntiles);
-  kernel<<<blocks, BLOCK, 0, st>>>(g);
+  // FP32 members with GF_MIXED's accumulator stage it in dynamic shared memory
+  const size_t smem = sizeof(R) == 4 ? acc_smem_bytes<LPT>() : 0;
+  kernel<<<blocks, BLOCK, smem, st>>>(g);
   return cudaGetLastError();
 }
 

@@ -44,7 +44,8 @@ static cudaError_t launch_kernel(const SweepArgs<R>& a, cudaStream_t st) {
   static const unsigned resident_staged = attr == cudaSuccess ? resident_blocks(kernel, smem_staged) : 0;
   const unsigned resident = staged ? resident_staged : resident_plain;
   const unsigned blocks = (unsigned)((resident && ntiles > resident) ? resident : ntiles);
-  kernel<<<blocks, BLOCK, staged ? smem_staged : 0, st>>>(a);
+  const size_t smem = staged ? smem_staged : (a.acc && a.obs == 0 ? acc_smem_bytes<LPT>() : 0);
+  kernel<<<blocks, BLOCK, smem, st>>>(a);
   return cudaGetLastError();
 }
 
