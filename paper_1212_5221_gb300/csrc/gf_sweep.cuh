@@ -1068,22 +1068,10 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R, GAUGE, LPT>())
   constexpr int NC = store_traits<R>::NC;
   constexpr int L = 8 / LPT;
   constexpr uint32_t TILE = BLOCK / L;
-  constexpr int WORDS = (int)(sizeof(SweepArgs<R>) / 4);
-  static_assert(sizeof(SweepArgs<R>) % 4 == 0 && WORDS <= BLOCK, "arguments copied word by word");
-  // the current member's arguments, copied to shared memory when the member changes
-  __shared__ __align__(16) SweepArgs<R> cur;
   const int lane = (int)(threadIdx.x % L);
   const uint32_t local = threadIdx.x / L;
-  uint32_t held = 0xffffffffu;
   for (uint64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
     const uint32_t m = group_member(g, tile);
-    if (m != held) {
-      __syncthreads();  // every thread is done with the previous member's arguments
-      if (threadIdx.x < WORDS)
-        reinterpret_cast<uint32_t*>(&cur)[threadIdx.x] = reinterpret_cast<const uint32_t*>(&g.m[m])[threadIdx.x];
-      __syncthreads();
-      held = m;
-    }
     const uint64_t next = tile + gridDim.x;
     if (next < g.ntiles && threadIdx.x < 9 * NC) {  // the next tile into L2, as the single-lattice kernel
       const uint32_t mn = group_member(g, next);
@@ -1096,7 +1084,9 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R, GAUGE, LPT>())
         prefetch_tile<R, GAUGE>(an, cn, sn, min(TILE, an.geom.Vh - sn), (int)threadIdx.x);
       }
     }
-    const SweepArgs<R>& a = cur;
+    // the member's arguments by value: the site's loads and stores cannot
+    // alias a private copy, so its fields stay in registers across them
+    const SweepArgs<R> a = g.m[m];
     const uint64_t t = tile - (m ? g.tile_end[m - 1] : 0);
     const uint32_t Vh = a.geom.Vh;
     const uint32_t tiles_per_copy = (Vh + TILE - 1) / TILE;
