@@ -1,6 +1,6 @@
 """The time-slab path (Sec. 5) on one GPU, through the C ABI.
 
-Several slabs of one lattice live in one process on the same stream and
+Several slabs of one lattice live in one process on one shared stream and
 exchange their boundary messages in memory, in the order the schedule of
 paper_1212_5221_gb300.slab uses (every slab updates its boundary slices and
 packs its messages, then the inner slices run, then every slab unpacks what
@@ -74,13 +74,18 @@ def _program_whole(gf, h, seed):
 def test_slabs_equal_whole_lattice(gf, synth, orc, gauge, prec, world):
     from paper_1212_5221_gb300 import slab
 
+    import torch
+
     lpt = 8 if prec == "fp64" else 4
     U = _field(synth, orc, DIMS)
     slabs = []
+    # the emulated processes hand their messages over in memory: one stream
+    # orders every slab's packs before the other slabs' unpacks
+    stream = torch.cuda.Stream()
     try:
         for r in range(world):
             t0, nt = slab.slab_bounds(DIMS[0], world, r)
-            s = slab.GpuSlab(DIMS, t0, nt, gauge, prec)
+            s = slab.GpuSlab(DIMS, t0, nt, gauge, prec, stream=stream)
             gf.gf_set_links_per_thread(s.h, lpt)
             s.load(U)
             slabs.append(s)
