@@ -769,11 +769,13 @@ int check_group(gf_ctx* const* ctxs, int n) {
   return GF_OK;
 }
 
-// One half-sweep (overrelaxation, omega) of members that share their
-// storage precision, as one launch on the first member's stream; the other
-// members' streams are ordered before and after it with events.
+// n sweeps (overrelaxation, omega) of members that share their storage
+// precision, one launch per half-sweep on the first member's stream.  The
+// arguments are built once and only the parity and the sweep index change
+// between launches; the other members' streams are ordered before the first
+// and after the last launch with events (not around every launch).
 template <typename R>
-int group_half_t(const std::vector<gf_ctx*>& m, double omega, int parity) {
+int group_sweeps_t(const std::vector<gf_ctx*>& m, double omega, int n) {
   gf_ctx* c0 = m[0];
   int lpt = default_lpt(c0, GF_OR);
   if (c0->gauge == GF_MAG && sizeof(R) == 8 && lpt == 8) lpt = 4;  // as the single-lattice launcher
@@ -782,7 +784,7 @@ int group_half_t(const std::vector<gf_ctx*>& m, double omega, int parity) {
   uint64_t cum = 0;
   for (size_t k = 0; k < m.size(); ++k) {
     // the group kernel prefetches the next tile into L2 or nothing (it has no staged form)
-    fill_args(g.m[k], m[k], gfk::ALG_OR, omega, parity, 0, (uint32_t)m[k]->sweep_index, 0, 1,
+    fill_args(g.m[k], m[k], gfk::ALG_OR, omega, 0, 0, 0, 0, 1,
               m[k]->prefetch == GF_PREFETCH_NONE ? GF_PREFETCH_NONE : GF_PREFETCH_L2, nullptr);
     cum += (uint64_t)((m[k]->G.Vh + tile - 1) / tile) * (uint64_t)m[k]->ncopies;
     g.tile_end[k] = cum;
@@ -797,11 +799,18 @@ int group_half_t(const std::vector<gf_ctx*>& m, double omega, int parity) {
       GF_CUDA(cudaStreamWaitEvent(c0->st, e, 0));
       evs.push_back(e);
     }
-  cudaEvent_t t0 = prof_begin(c0);
-  cudaError_t e = gfk::launch_group<R>(g, c0->gauge, lpt, c0->st);
-  if (e != cudaSuccess) return fail(GF_ECUDA, "group sweep launch: %s", cudaGetErrorString(e));
-  prof_end(c0, t0, sizeof(R) == 8 ? GF_KERNEL_SWEEP_FP64 : GF_KERNEL_SWEEP_FP32);
-  c0->launch_count++;
+  for (int s = 0; s < n; ++s)
+    for (int parity = 0; parity < 2; ++parity) {
+      for (size_t k = 0; k < m.size(); ++k) {
+        g.m[k].parity = parity;
+        g.m[k].sweep = (uint32_t)(m[k]->sweep_index + s);
+      }
+      cudaEvent_t t0 = prof_begin(c0);
+      cudaError_t e = gfk::launch_group<R>(g, c0->gauge, lpt, c0->st);
+      if (e != cudaSuccess) return fail(GF_ECUDA, "group sweep launch: %s", cudaGetErrorString(e));
+      prof_end(c0, t0, sizeof(R) == 8 ? GF_KERNEL_SWEEP_FP64 : GF_KERNEL_SWEEP_FP32);
+      c0->launch_count++;
+    }
   if (!evs.empty()) {
     cudaEvent_t done = take_event(c0);
     GF_CUDA(cudaEventRecord(done, c0->st));
@@ -815,19 +824,19 @@ int group_half_t(const std::vector<gf_ctx*>& m, double omega, int parity) {
   return GF_OK;
 }
 
-// One full sweep of every member: members in FP32 storage and members in
-// FP64 storage (a GF_MIXED member after its switch) go in separate launches.
-int group_sweep_once(const std::vector<gf_ctx*>& members, double omega) {
+// n sweeps of every member: members in FP32 storage and members in FP64
+// storage (a GF_MIXED member after its switch) go in separate launches.
+int group_sweeps(const std::vector<gf_ctx*>& members, double omega, int n) {
+  if (n <= 0) return GF_OK;
   std::vector<gf_ctx*> by[2];
   for (gf_ctx* c : members) by[c->fp64 ? 1 : 0].push_back(c);
-  for (int p = 0; p < 2; ++p)
-    for (int f = 0; f < 2; ++f) {
-      if (by[f].empty()) continue;
-      int r = f ? group_half_t<double>(by[f], omega, p) : group_half_t<float>(by[f], omega, p);
-      if (r) return r;
-    }
+  for (int f = 0; f < 2; ++f) {
+    if (by[f].empty()) continue;
+    int r = f ? group_sweeps_t<double>(by[f], omega, n) : group_sweeps_t<float>(by[f], omega, n);
+    if (r) return r;
+  }
   for (gf_ctx* c : members) {
-    c->sweep_index++;
+    c->sweep_index += (uint64_t)n;
     if (c->prec == GF_MIXED && !c->fp64) c->dirty = true;
   }
   return GF_OK;
@@ -1239,8 +1248,7 @@ int gf_group_sweep(gf_ctx* const* ctxs, int n, gf_algo algo, double param, int n
   if (n_sweeps < 0) return fail(GF_EINVAL, "n_sweeps < 0");
   std::vector<gf_ctx*> m(ctxs, ctxs + n);
   const double omega = algo == GF_RELAX ? 1.0 : param;
-  for (int k = 0; k < n_sweeps; ++k)
-    if ((r = group_sweep_once(m, omega))) return r;
+  if ((r = group_sweeps(m, omega, n_sweeps))) return r;
   for (gf_ctx* c : m) {
     if ((r = sync_master(c))) return r;
     GF_CUDA(cudaStreamSynchronize(c->st));
@@ -1326,16 +1334,24 @@ int gf_group_fix(gf_ctx* const* ctxs, int n, const gf_fix_params* P, gf_fix_resu
     int steps = P->check_interval;
     for (int k = 0; k < n; ++k)
       if (live[k]) steps = std::min(steps, std::max(1, P->max_sweeps - R[k].sweeps));
-    for (int s = 0; s < steps; ++s) {
-      if ((r = group_sweep_once(sweepers, omega))) return r;
+    for (int s = 0; s < steps;) {
+      // up to the next re-unitarisation of any sweeping member
+      int chunk = steps - s;
+      if (P->reunit_interval > 0)
+        for (int k = 0; k < n; ++k)
+          if (live[k] && std::find(sweepers.begin(), sweepers.end(), ctxs[k]) != sweepers.end())
+            chunk = std::min(chunk, P->reunit_interval - since[k]);
+      if ((r = group_sweeps(sweepers, omega, chunk))) return r;
+      s += chunk;
       for (int k = 0; k < n; ++k) {
         if (!live[k] || std::find(sweepers.begin(), sweepers.end(), ctxs[k]) == sweepers.end()) continue;
         gf_ctx* c = ctxs[k];
-        if (c->fp64) R[k].sweeps_fp64++;
-        else R[k].sweeps_fp32++;
-        R[k].sweeps++;
-        R[k].site_updates += units[k];
-        if (P->reunit_interval > 0 && ++since[k] >= P->reunit_interval) {
+        if (c->fp64) R[k].sweeps_fp64 += chunk;
+        else R[k].sweeps_fp32 += chunk;
+        R[k].sweeps += chunk;
+        R[k].site_updates += (uint64_t)chunk * units[k];
+        since[k] += chunk;
+        if (P->reunit_interval > 0 && since[k] >= P->reunit_interval) {
           since[k] = 0;
           if ((r = reunitarize(c))) return r;
         }
