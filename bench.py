@@ -761,7 +761,9 @@ def run_config3_study(args):
     torch.cuda.synchronize()
     out = {"lattice": "64^3x256", "switch_theta": 1e-8, "theta_target": 1e-12}
     logdir = os.path.join(ROOT, "gpurun_out")
-    for gauge, omega, cap in (("coulomb", 1.7, args.study_iters), ("landau", args.config3_omega, args.study_iters)):
+    runs = [("coulomb", 1.7), ("landau", args.config3_omega)]
+    for gauge, omega in [r for r in runs if r[0] in args.config3_gauges.split(",")]:
+        cap = args.study_iters
         h = gf.gf_create(dims, gauge, "mixed")
         if os.path.isdir(logdir):
             gf.gf_set_check_log(h, os.path.join(logdir, f"config3_{gauge}_checks.jsonl"))
@@ -932,6 +934,7 @@ def main():
     ap.add_argument("--study-every", type=int, default=2000)
     ap.add_argument("--config3-omega", type=float, default=1.7,
                     help="overrelaxation parameter of the 64^3x256 Landau fix (Coulomb uses 1.7)")
+    ap.add_argument("--config3-gauges", default="coulomb,landau", help="which config-3 fixes to run")
     ap.add_argument("--config4-sa-steps", type=int, default=3000)
     args = ap.parse_args()
     if args.study == "precision":
