@@ -518,6 +518,14 @@ def run_serving(args):
                 results += gf.gf_server_poll(srv, 256, 1000)
         finally:
             gf.gf_server_destroy(srv)
+        if args.serve_log:
+            with open(args.serve_log, "a") as f:
+                for r in sorted(results, key=lambda x: x["tag"]):
+                    j = jobs[r["tag"]]
+                    f.write(json.dumps({"rate": rate, "tag": r["tag"], "dims": j["dims"], "gauge": j["gauge"],
+                                        "status": r["status"], "sweeps": r["sweeps"], "theta": r["theta"],
+                                        "latency_s": r["t_done"] - r["t_submit"],
+                                        "queue_s": r["t_admit"] - r["t_submit"]}) + "\n")
         bad = [r for r in results if r["status"] not in (0, gf.GF_ENOTCONV)]
         if bad:
             raise RuntimeError(f"{len(bad)} jobs failed, first status {bad[0]['status']}")
@@ -540,7 +548,10 @@ def run_serving(args):
                     sweeps=sum(r["sweeps"] for r in results))
 
     with Clocks(0) as clocks:
-        sat = run(0.0, min(args.serve_sat_jobs, n))
+        if args.serve_rate > 0:  # the saturated rate measured before, given
+            sat = {"jobs_per_s": args.serve_rate, "given": True}
+        else:
+            sat = run(0.0, min(args.serve_sat_jobs, n))
         log("saturated:", json.dumps(sat))
         loads = []
         for f in args.serve_loads:
@@ -923,6 +934,9 @@ def main():
     ap.add_argument("--serve-max-sweeps", type=int, default=20000)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-sat-jobs", type=int, default=100, help="jobs of the saturated-rate run")
+    ap.add_argument("--serve-rate", type=float, default=0.0,
+                    help="a saturated rate (jobs/s) measured before: skips the saturated run")
+    ap.add_argument("--serve-log", default=None, help="append one JSON line per job to this file")
     ap.add_argument("--serve-mag-sa", type=int, default=300, help="annealing steps of a MAG job")
     ap.add_argument("--serve-mag-sr", type=int, default=1000, help="most stochastic-relaxation sweeps of a MAG job")
     ap.add_argument("--serve-loads", type=lambda v: [float(x) for x in v.split(",") if x], default=[0.7],
