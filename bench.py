@@ -870,6 +870,55 @@ def run_group_study(args):
     print(json.dumps({"study": "group", **out}), flush=True)
 
 
+def run_slab(args, rank, world, local_rank):
+    """One lattice split into time slabs over the ranks (Sec. 5; one process
+    per GPU under torchrun, NCCL boundary exchange after every half-sweep):
+    the 32^3x64 workload's field at the orbit point of seed 1000, --slab-sweeps
+    overrelaxation sweeps (omega 1.7) in --slab-precision storage, timed with
+    CUDA events between barriers; rank 0 prints one JSON line (strong
+    scaling: the lattice is fixed, the ranks share it)."""
+    import torch
+
+    from paper_1212_5221_gb300 import build, gf, inputs, slab
+
+    build.build_all()
+    W = WORKLOAD
+    dims = W["dims"]
+    t0, nt = slab.slab_bounds(dims[0], world, rank)
+    U = inputs.links(dims, "smooth", W["eps"], W["field_seed"])
+    s = slab.GpuSlab(dims, t0, nt, W["gauge"], args.slab_precision)
+    h = gf.gf_create(dims, W["gauge"], "fp64")  # the orbit point, made once on this rank's GPU
+    gf.gf_load_links(h, 0, U)
+    gf.gf_random_gauge_transform(h, 1000)
+    gf.gf_store_links(h, 0, U)
+    gf.gf_destroy(h)
+    s.load(U)
+    ts = slab.TimeSlab(s, slab.Ring(), nt, dims[0], W["gauge"])
+    ts.sweep("or", W["omega"], 2)  # warm-up
+    dist = torch.distributed.is_initialized()
+    if dist:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(s.stream)
+    ts.sweep("or", W["omega"], args.slab_sweeps)
+    stop.record(s.stream)
+    torch.cuda.synchronize()
+    elapsed = start.elapsed_time(stop) / 1e3
+    F, theta = ts.functional_theta()
+    elapsed_all, su_all = reduce_over_ranks(elapsed, float(nt * np.prod(dims[1:]) * args.slab_sweeps),
+                                            torch.device("cuda", local_rank) if dist else None)
+    s.close()
+    if rank == 0:
+        print(json.dumps({"metric": "site-updates/s (one lattice in time slabs)", "value": su_all / elapsed_all,
+                          "unit": "site-updates/s", "n_gpus": world, "steps": args.slab_sweeps, "warmup": 2,
+                          "ms_per_step": elapsed_all / args.slab_sweeps * 1e3, "higher_is_better": True,
+                          "scaling": "strong", "dtype": "f64" if args.slab_precision == "fp64" else "f32",
+                          "data": "synthetic", "F": F, "theta": theta,
+                          "config": {"workload": "landau_or_32c3x64_timeslabs", "slabs": world, "slices_per_slab": nt,
+                                     "precision": args.slab_precision, "omega": W["omega"]}}), flush=True)
+
+
 def run_kernel_target(args):
     """Short, fixed launch sequences on the workload's lattice for ncu captures.
     fp32 / fp64 / mixed: 3 sweeps in that precision (mixed: FP32 sweeps that
@@ -929,6 +978,10 @@ def main():
                     default=None,
                     help="only run a short, fixed launch sequence of the workload (for ncu)")
     ap.add_argument("--serving", action="store_true", help="run the serving workload (job p50/p99)")
+    ap.add_argument("--slab", action="store_true",
+                    help="one lattice in time slabs over the ranks (strong scaling) instead of replicas")
+    ap.add_argument("--slab-sweeps", type=int, default=200)
+    ap.add_argument("--slab-precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--serve-theta", type=float, default=1e-10)
     ap.add_argument("--serve-max-sweeps", type=int, default=20000)
@@ -994,7 +1047,10 @@ def main():
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    run_ours(args, rank, world, local_rank)
+    if args.slab:
+        run_slab(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
     if world > 1:
         import torch
 
