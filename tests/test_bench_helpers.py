@@ -69,4 +69,4 @@ def test_bench_help_without_gpu():
 
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"], capture_output=True, text=True,
                        timeout=120)
-    assert r.returncode == 0 and "--serving" in r.stdout and "--study" in r.stdout
+    assert r.returncode == 0 and "--serving" in r.stdout and "--study" in r.stdout and "--slab" in r.stdout
