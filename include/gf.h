@@ -205,7 +205,9 @@ enum { GF_SLAB_OWNED = 0, GF_SLAB_BOUNDARY = 1, GF_SLAB_INNER = 2 };
  * except that GF_SA is the heat bath alone.  Draws use the context's sweep
  * index, which this call leaves unchanged (advance it with
  * gf_set_sweep_index once both halves are done).  Enqueued on the context's
- * stream; returns without waiting. */
+ * stream; returns without waiting.  In FP64 storage each launch covers only
+ * its part's sites (GF_SLAB_BOUNDARY: one launch per boundary slice), spread
+ * over the whole grid; FP32 launches cover the slab and skip other slices. */
 int gf_sweep_half(gf_ctx* ctx, gf_algo algo, double param, int parity, int part, uint64_t seed);
 
 /* Bytes of one boundary message: 3 (FP32) or 6 (FP64) x Nx*Ny*Nz/2 x 16. */

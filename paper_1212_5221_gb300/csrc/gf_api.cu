@@ -294,15 +294,23 @@ void fill_args(gfk::SweepArgs<R>& a, gf_ctx* c, int kalgo, double param, int par
   a.wait_polls = sizeof(R) == 8 ? -1 : c->stage_wait_polls;
   a.sa_trace = kalgo == gfk::ALG_SA ? c->sa_trace_d : nullptr;
   a.site_offset = c->site_offset;
+  a.sp_lo = 0;
+  a.sp_n = c->G.Vh;
 }
 
+// sp_lo, sp_n: the sites of each copy an FP64 launch covers (all by default).
 int launch_half(gf_ctx* c, int kalgo, double param, int parity, uint64_t seed, uint32_t sweep, int lpt,
-                int obs = 0, int update = 1, int pmode = -1, const int* active_override = nullptr) {
+                int obs = 0, int update = 1, int pmode = -1, const int* active_override = nullptr,
+                uint32_t sp_lo = 0, uint32_t sp_n = UINT32_MAX) {
   const int prefetch = pmode >= 0 ? pmode : c->prefetch;
   cudaError_t e;
   if (c->fp64) {
     gfk::SweepArgs<double> a;
     fill_args(a, c, kalgo, param, parity, seed, sweep, obs, update, prefetch, active_override);
+    if (sp_n != UINT32_MAX) {
+      a.sp_lo = sp_lo;
+      a.sp_n = sp_n;
+    }
     cudaEvent_t t0 = prof_begin(c);
     e = gfk::launch_sweep<double>(a, c->gauge, kalgo, lpt, c->st);
     prof_end(c, t0, GF_KERNEL_SWEEP_FP64);
@@ -1199,10 +1207,22 @@ int gf_sweep_half(gf_ctx* c, gf_algo algo, double param, int parity, int part, u
   const double p = algo == GF_RELAX ? 1.0 : algo == GF_MICRO ? 0.0 : param;
   const int* act = c->slab ? c->slab_flags_d + (size_t)part * c->dims[0] : nullptr;
   const int pm = c->pmode[c->fp64][algo] - 1;
-  r = launch_half(c, kalgo, p, parity ^ c->parity_flip, seed, (uint32_t)c->sweep_index, default_lpt(c, algo), 0, 1,
-                  pm, act);
-  if (r) return r;
-  return GF_OK;
+  const int lp = default_lpt(c, algo);
+  const uint32_t sw = (uint32_t)c->sweep_index;
+  if (!(c->slab && c->fp64))
+    return launch_half(c, kalgo, p, parity ^ c->parity_flip, seed, sw, lp, 0, 1, pm, act);
+  // FP64 slab: each launch covers its slices' sites only (slice t holds the
+  // sites [t, t + 1) x V3/2 of a parity), so that the FP64 kernel's equal
+  // ranges spread the part over every block; the flags stay as a guard
+  const uint32_t vs = (uint32_t)(c->G.V3 / 2), nl = (uint32_t)c->dims[0];
+  if (part == GF_SLAB_BOUNDARY) {
+    for (uint32_t t : {1u, nl - 2u})
+      if ((r = launch_half(c, kalgo, p, parity ^ c->parity_flip, seed, sw, lp, 0, 1, pm, act, t * vs, vs))) return r;
+    return GF_OK;
+  }
+  const uint32_t t0 = part == GF_SLAB_INNER ? 2u : 1u, t1 = part == GF_SLAB_INNER ? nl - 2u : nl - 1u;  // [t0, t1)
+  if (t1 <= t0) return GF_OK;  // two owned slices: no inner slice
+  return launch_half(c, kalgo, p, parity ^ c->parity_flip, seed, sw, lp, 0, 1, pm, act, t0 * vs, (t1 - t0) * vs);
 }
 
 int gf_slab_bytes(gf_ctx* c, size_t* bytes) {

@@ -36,6 +36,10 @@ struct SweepArgs {
                       // trial counts (0 = none accepted; MAG: 1), written by lane 0
   uint32_t site_offset;  // added to the site index in the Philox counters (time slabs: the
                          // global index of a local site)
+  uint32_t sp_lo, sp_n;  // FP64 storage: the launch covers sites [sp_lo, sp_lo + sp_n) of
+                         // each copy (0, Vh for all; a time-slab part its slices).  The
+                         // FP32 kernels deal whole tiles round-robin over all Vh sites,
+                         // which spreads any set of active slices over every block already
 };
 
 // Per-site FP64 observables of the MAG form from the slot matrices M
@@ -1000,23 +1004,30 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<R, GAUGE, LPT, MP>()) sweep_
   if constexpr (sizeof(R) == 8) {
     // FP64 is ALU-bound: every block takes an equal contiguous range of the
     // (copy, site) indices in tiles of TILE, so that no SM finishes a whole
-    // tile before the others (whole tiles dealt round-robin left a 4 % tail)
-    const uint64_t total = (uint64_t)Vh * a.ncopies;
+    // tile before the others (whole tiles dealt round-robin left a 4 % tail).
+    // The indices run over the launch's sites [sp_lo, sp_lo + sp_n) of each
+    // copy, so that a part of the lattice (a time slab's boundary slice) is
+    // spread over every block too.
+    const uint32_t span = a.sp_n;
+    const uint64_t total = (uint64_t)span * a.ncopies;
     const uint64_t lo = total * blockIdx.x / gridDim.x, hi = total * (blockIdx.x + 1) / gridDim.x;
-    // (copy, site) of the tile's first index, advanced by TILE per iteration
-    uint32_t c0 = (uint32_t)(lo / Vh), s0 = (uint32_t)(lo - (uint64_t)c0 * Vh);
+    // (copy, offset in the range) of the tile's first index, advanced by TILE
+    // per iteration
+    uint32_t c0 = span ? (uint32_t)(lo / span) : 0u;
+    uint32_t s0 = (uint32_t)(lo - (uint64_t)c0 * span);
     for (uint64_t base = lo; base < hi; base += TILE) {
       if (a.prefetch && base + TILE < hi && threadIdx.x < 9 * NC) {
         uint32_t nc = c0, ns = s0 + TILE;
-        while (ns >= Vh) ns -= Vh, ++nc;
-        const uint32_t n = (uint32_t)min((uint64_t)min(TILE, Vh - ns), hi - base - TILE);
-        prefetch_tile<R, GAUGE>(a, nc, ns, n, (int)threadIdx.x);
+        while (ns >= span) ns -= span, ++nc;
+        const uint32_t n = (uint32_t)min((uint64_t)min(TILE, span - ns), hi - base - TILE);
+        prefetch_tile<R, GAUGE>(a, nc, a.sp_lo + ns, n, (int)threadIdx.x);
       }
       uint32_t copy = c0, sp = s0 + local;
-      while (sp >= Vh) sp -= Vh, ++copy;
+      while (sp >= span) sp -= span, ++copy;
+      sp += a.sp_lo;
       site_dispatch<R, GAUGE, ALGO, LPT, OBS, MP>(a, copy, sp, base + local < hi, lane, nullptr, sp);
       s0 += TILE;
-      while (s0 >= Vh) s0 -= Vh, ++c0;
+      while (s0 >= span) s0 -= span, ++c0;
     }
   } else {
     // FP32 is HBM-bound: whole tiles dealt round-robin keep the blocks' reads

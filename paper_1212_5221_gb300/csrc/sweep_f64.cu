@@ -21,10 +21,11 @@ static unsigned resident_blocks(K kernel) {
 template <typename R, int GAUGE, int ALGO, int LPT, bool OBS>
 static cudaError_t launch_kernel(const SweepArgs<R>& a, cudaStream_t st) {
   constexpr uint32_t TILE = BLOCK / (8 / LPT);
-  const uint64_t ntiles = (uint64_t)((a.geom.Vh + TILE - 1) / TILE) * a.ncopies;
+  const uint64_t ntiles = (uint64_t)((a.sp_n + TILE - 1) / TILE) * a.ncopies;  // the launch's site range
   auto kernel = sweep_kernel<R, GAUGE, ALGO, LPT, OBS>;
   static const unsigned resident = resident_blocks(kernel);
   const unsigned blocks = (unsigned)((resident && ntiles > resident) ? resident : ntiles);
+  if (blocks == 0) return cudaSuccess;  // an empty range
   kernel<<<blocks, BLOCK, 0, st>>>(a);
   return cudaGetLastError();
 }
