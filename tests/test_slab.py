@@ -153,6 +153,66 @@ def test_process_slabs_equal_whole_lattice(orc, synth, gauge, world):
         assert abs(thr - th) <= 1e-12 * abs(th)
 
 
+def _fix_worker(rank, world, port, gauge, q):
+    import sys
+
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        from paper_1212_5221_gb300 import slab
+
+        oracle.build()
+        U = _field(gauge)
+        t0, nt = slab.slab_bounds(DIMS[0], world, rank)
+        be = OracleSlab(oracle, U, t0, nt, gauge)
+        ts = slab.TimeSlab(be, slab.Ring(), nt, DIMS[0], gauge)
+        n, F, th = ts.fix("or", FIX["omega"], FIX["theta"], max_sweeps=FIX["max"], check_interval=FIX["check"],
+                          reunit_interval=FIX["reunit"])
+        q.put((rank, t0, be.U[t0:t0 + nt].copy(), n, F, th))
+    finally:
+        dist.destroy_process_group()
+
+
+FIX = dict(omega=1.7, theta=1e-10, max=4000, check=10, reunit=50)
+
+
+def test_process_slabs_fix(orc, synth):
+    """The schedule's convergence loop on two processes: every process stops
+    after the same sweep count, decided on the FP64 theta reduced over both;
+    that count, the links and F equal the same loop (checks every 10 sweeps,
+    re-unitarisation every 50) on the whole lattice."""
+    world, gauge = 2, "landau"
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_fix_worker, args=(r, world, port, gauge, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=600) for _ in range(world)]
+    for p in procs:
+        p.join(60)
+        assert p.exitcode == 0
+    W = _field(gauge)
+    done = since = 0
+    while True:
+        F, th, _, _ = orc.observables(W, gauge)
+        if th < FIX["theta"] or done >= FIX["max"]:
+            break
+        orc.sweep(W, gauge, "or", FIX["omega"], FIX["check"], done)
+        done += FIX["check"]
+        since += FIX["check"]
+        if since >= FIX["reunit"]:
+            orc.reunitarize(W)
+            since = 0
+    assert th < FIX["theta"] and done > 0
+    for rank, t0, owned, n, Fr, thr in out:
+        assert n == done, rank
+        assert np.array_equal(owned, W[t0:t0 + owned.shape[0]]), rank
+        assert abs(Fr - F) <= 1e-14 * abs(F) and abs(thr - th) <= 1e-9 * th
+
+
 def test_one_process_slab_equals_whole_lattice(orc, synth):
     """World size 1: the process is its own neighbour (halo = its last slice)."""
     from paper_1212_5221_gb300 import slab
