@@ -1339,7 +1339,7 @@ int gf_group_fix(gf_ctx* const* ctxs, int n, const gf_fix_params* P, gf_fix_resu
       }
       if (!c->fp64 && c->prec == GF_MIXED && (worst < P->switch_theta || !std::isfinite(worst))) {
         if ((r = promote(c))) return r;
-        continue;  // evaluated again in FP64 at the next round
+        continue;  // evaluated again in FP64 at the next pass of the loop
       }
       sweepers.push_back(c);
       units[k] = (uint64_t)n_active * (coul ? c->G.V3 : c->G.V);
@@ -1348,7 +1348,7 @@ int gf_group_fix(gf_ctx* const* ctxs, int n, const gf_fix_params* P, gf_fix_resu
       bool any = false;
       for (int k = 0; k < n; ++k) any = any || live[k];
       if (!any) break;
-      continue;  // only promotions this round
+      continue;  // only promotions in this pass
     }
     // a common interval: the members that are still sweeping
     int steps = P->check_interval;
